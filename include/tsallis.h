@@ -1,0 +1,184 @@
+/*
+ * tsallis.h -- C ABI of the GB300 maximum-Tsallis-entropy thresholding path.
+ *
+ * The method (Chang & Sheu, "GPU acceleration of a patient-specific airway
+ * image segmentation and its assessment", section II-C "Segmentation"):
+ *   1. histogram of grey levels (section I "Thresholding", Fig. 2), or the
+ *      2-D histogram of grey level x 3x3(x3) floor-mean level (section II-C,
+ *      "Tsallis entropy", the mean-image and h(i, j) equations);
+ *   2. class masses P_1, P_2 and class Tsallis entropies H_1^alpha, H_2^alpha
+ *      for every threshold t (or pair (t, s));
+ *   3. the pseudo-additive objective
+ *          phi_alpha = H_1 + H_2 + (1 - alpha) H_1 H_2,
+ *      maximised over all thresholds;
+ *   4. Algorithm 1 (thresholding kernel): every voxel is set to 1 or 0 by
+ *      comparing its level with the chosen threshold.
+ * alpha is called q below.
+ *
+ * Conventions shared by every entry point:
+ *   - All device pointers are plain CUDA device addresses owned by the
+ *     caller. The library never frees them and keeps no reference after the
+ *     call returns. Work is enqueued on the given stream and runs
+ *     asynchronously; results are valid after the stream is synchronised.
+ *   - Volumes are int16 Hounsfield values laid out [nz][ny][nx], x fastest,
+ *     contiguous. Masks are uint8 [nz][ny][nx] holding 0 or 1.
+ *   - Volume and mask base pointers must be 16-byte aligned (any cudaMalloc
+ *     result is); otherwise TSALLIS_ERR_ALIGNMENT is returned. Any nx, ny, nz
+ *     is accepted; ragged tails are handled inside the kernels.
+ *   - Argument, size and alignment errors are returned synchronously, before
+ *     anything is enqueued. Data-dependent outcomes (no valid threshold, a
+ *     device wait that ran out) are written per histogram to d_status and are
+ *     read after synchronising.
+ *   - A context owns scratch memory on its device. Calls on one context must
+ *     not overlap in time on different streams (they share that scratch).
+ *     Contexts are independent of each other.
+ */
+#ifndef TSALLIS_H
+#define TSALLIS_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TSALLIS_OK = 0,
+    TSALLIS_ERR_INVALID_ARG = 1,       /* null pointer, bad size, q <= 0 or not finite, ... */
+    TSALLIS_ERR_ALIGNMENT = 2,         /* a volume or mask pointer is not 16-byte aligned */
+    TSALLIS_ERR_CUDA = 3,              /* a CUDA runtime call failed */
+    TSALLIS_ERR_NO_VALID_THRESHOLD = 4,/* per histogram: fewer than two non-empty levels */
+    TSALLIS_ERR_TIMEOUT = 5,           /* per histogram: a bounded device wait ran out */
+    TSALLIS_ERR_OOM = 6,               /* scratch allocation failed */
+    TSALLIS_ERR_UNIMPLEMENTED = 7
+} tsallis_status;
+
+/* Extra bits OR-ed into d_status entries (low byte holds a tsallis_status). */
+#define TSALLIS_STATUS_RERANKED 0x100  /* FP64 re-rank decided between near-tied candidates */
+
+typedef enum {
+    TSALLIS_PER_SLICE = 0,    /* one histogram and threshold per z slice */
+    TSALLIS_WHOLE_VOLUME = 1  /* one histogram and threshold for the whole volume */
+} tsallis_mode;
+
+typedef enum {
+    TSALLIS_MASK_LOW = 0,  /* mask = 1 where level <= t (class 1: the low-HU lumen) */
+    TSALLIS_MASK_HIGH = 1  /* mask = 1 where level >= t + 1 (Algorithm 1 with T = t + 1) */
+} tsallis_polarity;
+
+/* Debug flags (tests only). */
+#define TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL 0x1u /* the first histogram tile never reports
+                                                arrival, so waits on its histogram run out */
+
+typedef struct {
+    int32_t lo;       /* Hounsfield value of level 0; default -1024 */
+    int32_t nbins;    /* L, number of 1-D levels, 2..4096; default 4096. Level of a
+                         voxel v is b = clamp(v - lo, 0, L - 1). */
+    float q;          /* Tsallis index (alpha), > 0 and finite; q == 1 selects the
+                         Shannon (Kapur) limit. Default 0.8 */
+    int32_t mode;     /* tsallis_mode; default TSALLIS_PER_SLICE */
+    int32_t polarity; /* tsallis_polarity; default TSALLIS_MASK_LOW */
+    int32_t two_d;    /* 0: 1-D form; 1: 2-D grey x mean form. Default 0 */
+    int32_t shift;    /* 2-D only: grey level = b >> shift, giving L2 = nbins >> shift
+                         levels (2..256); default 4 */
+    int32_t topk;     /* 0: exhaustive search (default) */
+    uint32_t flags;   /* TSALLIS_FLAG_* */
+} tsallis_params;
+
+typedef struct tsallis_ctx tsallis_ctx;
+
+/* Fills p with the defaults listed above. */
+tsallis_status tsallis_params_default(tsallis_params* p);
+
+/* Human-readable name of a status code (the low byte of d_status entries). */
+const char* tsallis_status_string(int32_t status);
+
+/* Creates a context bound to CUDA device `device`. *ctx receives the handle.
+ * Allocates nothing on the device until the first call that needs scratch. */
+tsallis_status tsallis_create(tsallis_ctx** ctx, int device);
+
+/* Releases the context's scratch memory. Safe with NULL. The caller must
+ * make sure no work of this context is still running. */
+void tsallis_destroy(tsallis_ctx* ctx);
+
+/* Limit, in nanoseconds, on every device-side wait of this context
+ * (default 1e9). A wait that runs out writes TSALLIS_ERR_TIMEOUT. */
+tsallis_status tsallis_set_wait_timeout(tsallis_ctx* ctx, uint64_t ns);
+
+/*
+ * Step 1: histogram (section I "Thresholding", Fig. 2; 2-D: section II-C,
+ * mean image g and h(i, j)).
+ *   d_vol   [nz][ny][nx] int16, device.
+ *   d_hist  out, int32, device: 1-D: [nh][nbins]; 2-D: [nh][L2][L2] indexed
+ *           [grey][mean]. nh = nz (per slice) or 1 (whole volume).
+ *           Overwritten (zeroed first).
+ * 2-D per-slice mode uses the 3x3 in-slice mean (the paper's form); 2-D
+ * whole-volume mode uses the 3x3x3 mean when nz > 1. Both clamp indices at
+ * the borders. Counts per histogram must stay below 2^31.
+ */
+tsallis_status tsallis_histogram(tsallis_ctx* ctx, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                                 const tsallis_params* p, int32_t* d_hist, cudaStream_t stream);
+
+/*
+ * Steps 2-3: objective over every threshold and its maximiser (section II-C,
+ * class-mass, class-entropy and phi_alpha equations), for nh histograms.
+ *   d_hist    [nh][nbins] (1-D) or [nh][L2][L2] (2-D) int32, device.
+ *   d_t       out, int32: 1-D: [nh] threshold t; 2-D: [nh][2] pairs (t, s).
+ *             t = -1 when no threshold is valid.
+ *   d_phi     out, float [nh]: maximum objective value.
+ *   d_status  out, int32 [nh]: tsallis_status | TSALLIS_STATUS_* bits.
+ *   d_curve   optional out (may be NULL), float: 1-D [nh][nbins-1] phi(t);
+ *             2-D [nh][L2-1][L2-1] phi(t, s). NaN where a class is empty.
+ * t (then s) is the smallest maximiser. Objective values are FP32 with
+ * compensated sums; candidates within the FP32 error band of the maximum are
+ * re-ranked in FP64.
+ */
+tsallis_status tsallis_search(tsallis_ctx* ctx, const int32_t* d_hist, int64_t nh, const tsallis_params* p,
+                              int32_t* d_t, float* d_phi, int32_t* d_status, float* d_curve,
+                              cudaStream_t stream);
+
+/*
+ * Step 4: Algorithm 1 (thresholding kernel) with thresholds from d_t
+ * (per slice: [nz]; whole volume: [1]; 2-D: pairs, only t is used, applied
+ * to the grey level b >> shift). t = -1 gives an all-zero mask.
+ *   d_mask  out, uint8 [nz][ny][nx], device.
+ */
+tsallis_status tsallis_binarize(tsallis_ctx* ctx, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                                const int32_t* d_t, const tsallis_params* p, uint8_t* d_mask,
+                                cudaStream_t stream);
+
+/*
+ * Steps 1-4 fused in one persistent kernel (1-D form): per-slice histograms
+ * are built, searched by the last tile to arrive, and the slice is binarised
+ * while it is still in L2.
+ *   d_mask out [nz][ny][nx]; d_t, d_phi, d_status out [nh] as in
+ *   tsallis_search (nh = nz per slice, 1 whole volume).
+ * The 2-D form is dispatched to its own kernels by the same call.
+ */
+tsallis_status tsallis_segment(tsallis_ctx* ctx, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                               const tsallis_params* p, uint8_t* d_mask, int32_t* d_t, float* d_phi,
+                               int32_t* d_status, cudaStream_t stream);
+
+/* One volume of a batch: device pointers and its shape. */
+typedef struct {
+    const int16_t* vol;
+    uint8_t* mask;
+    int64_t nx, ny, nz;
+} tsallis_volume;
+
+/*
+ * Steps 1-4 for nvol volumes of uneven depth in one persistent launch, one
+ * histogram and threshold per volume (whole-volume mode) or per slice
+ * (per-slice mode, slices of all volumes numbered consecutively).
+ *   h_vols   host array of nvol descriptors (read during the call only).
+ *   d_t, d_phi, d_status  out, one entry per histogram.
+ */
+tsallis_status tsallis_segment_batch(tsallis_ctx* ctx, const tsallis_volume* h_vols, int32_t nvol,
+                                     const tsallis_params* p, int32_t* d_t, float* d_phi, int32_t* d_status,
+                                     cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSALLIS_H */

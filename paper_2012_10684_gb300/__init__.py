@@ -1,0 +1,271 @@
+"""GB300 maximum-Tsallis-entropy threshold segmentation.
+
+Thin Python binding of the C ABI declared in ``include/tsallis.h``
+(``libtsallis.so``, built in-tree by :mod:`paper_2012_10684_gb300.build`).
+Functions carry the C names and only marshal arguments: torch tensors supply
+device memory and the current CUDA stream; every step of the path runs in the
+library's CUDA kernels. There is no CPU fallback: if the library is missing,
+every call raises.
+
+Method (Chang & Sheu, section II-C "Segmentation"): histogram of grey levels,
+class masses and Tsallis class entropies for every threshold, the
+pseudo-additive objective H1 + H2 + (1 - q) H1 H2 maximised over all
+thresholds, then Algorithm 1 (thresholding kernel) on every voxel.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "Params", "TsallisError", "lib", "tsallis_params", "tsallis_histogram", "tsallis_search",
+    "tsallis_binarize", "tsallis_segment", "tsallis_segment_batch", "tsallis_status_string",
+    "TSALLIS_OK", "TSALLIS_ERR_NO_VALID_THRESHOLD", "TSALLIS_ERR_TIMEOUT", "TSALLIS_STATUS_RERANKED",
+]
+
+TSALLIS_OK = 0
+TSALLIS_ERR_INVALID_ARG = 1
+TSALLIS_ERR_ALIGNMENT = 2
+TSALLIS_ERR_CUDA = 3
+TSALLIS_ERR_NO_VALID_THRESHOLD = 4
+TSALLIS_ERR_TIMEOUT = 5
+TSALLIS_ERR_OOM = 6
+TSALLIS_ERR_UNIMPLEMENTED = 7
+TSALLIS_STATUS_RERANKED = 0x100
+TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL = 0x1
+
+PER_SLICE, WHOLE_VOLUME = 0, 1
+MASK_LOW, MASK_HIGH = 0, 1
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``tsallis_params``."""
+    _fields_ = [("lo", ctypes.c_int32), ("nbins", ctypes.c_int32), ("q", ctypes.c_float),
+                ("mode", ctypes.c_int32), ("polarity", ctypes.c_int32), ("two_d", ctypes.c_int32),
+                ("shift", ctypes.c_int32), ("topk", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class Volume(ctypes.Structure):
+    """Mirror of ``tsallis_volume``."""
+    _fields_ = [("vol", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
+
+
+class TsallisError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (fn, tsallis_status_string(code), code))
+
+
+_lock = threading.Lock()
+_lib = None
+_ctx = {}
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = {
+    "tsallis_params_default": ([ctypes.POINTER(Params)], ctypes.c_int),
+    "tsallis_status_string": ([ctypes.c_int32], ctypes.c_char_p),
+    "tsallis_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int], ctypes.c_int),
+    "tsallis_destroy": ([_P], None),
+    "tsallis_set_wait_timeout": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "tsallis_histogram": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(Params), _P, _P], ctypes.c_int),
+    "tsallis_search": ([_P, _P, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
+    "tsallis_binarize": ([_P, _P, _I64, _I64, _I64, _P, ctypes.POINTER(Params), _P, _P], ctypes.c_int),
+    "tsallis_segment": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
+    "tsallis_segment_batch": ([_P, ctypes.POINTER(Volume), ctypes.c_int32, ctypes.POINTER(Params), _P, _P, _P, _P],
+                              ctypes.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded C-ABI library. Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libtsallis.so is not built (run paper_2012_10684_gb300.build.build()); "
+                                   "there is no CPU fallback")
+            L = ctypes.CDLL(_build.LIB)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def tsallis_status_string(code: int) -> str:
+    try:
+        return lib().tsallis_status_string(int(code)).decode()
+    except RuntimeError:
+        return "status %d" % code
+
+
+def _check(fn, rc):
+    if rc != TSALLIS_OK:
+        raise TsallisError(fn, rc)
+
+
+def context(device=None) -> int:
+    """Handle of the per-device context (created on first use)."""
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+    if dev is None:
+        dev = torch.cuda.current_device()
+    with _lock:
+        h = _ctx.get(dev)
+    if h is None:
+        p = ctypes.c_void_p()
+        _check("tsallis_create", lib().tsallis_create(ctypes.byref(p), dev))
+        with _lock:
+            _ctx[dev] = p.value
+        h = p.value
+    return h
+
+
+def set_wait_timeout(ns: int, device=None) -> None:
+    _check("tsallis_set_wait_timeout", lib().tsallis_set_wait_timeout(context(device), int(ns)))
+
+
+def tsallis_params(q: float = 0.8, lo: int = -1024, nbins: int = 4096, mode="slice", polarity="low",
+                   two_d: bool = False, shift: int = 4, topk: int = 0, flags: int = 0) -> Params:
+    p = Params()
+    lib().tsallis_params_default(ctypes.byref(p))
+    p.q, p.lo, p.nbins = float(q), int(lo), int(nbins)
+    p.mode = {"slice": PER_SLICE, "volume": WHOLE_VOLUME, PER_SLICE: PER_SLICE, WHOLE_VOLUME: WHOLE_VOLUME}[mode]
+    p.polarity = {"low": MASK_LOW, "high": MASK_HIGH, MASK_LOW: MASK_LOW, MASK_HIGH: MASK_HIGH}[polarity]
+    p.two_d, p.shift, p.topk, p.flags = int(bool(two_d)), int(shift), int(topk), int(flags)
+    return p
+
+
+def _vol3(vol: torch.Tensor):
+    if not isinstance(vol, torch.Tensor) or not vol.is_cuda:
+        raise TypeError("volume must be a CUDA tensor")
+    if vol.dtype != torch.int16 or not vol.is_contiguous():
+        raise TypeError("volume must be a contiguous int16 tensor")
+    if vol.dim() == 2:
+        return vol.shape[1], vol.shape[0], 1
+    if vol.dim() != 3:
+        raise ValueError("volume must be [nz][ny][nx] or [ny][nx]")
+    return vol.shape[2], vol.shape[1], vol.shape[0]
+
+
+def _stream(t: torch.Tensor) -> int:
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def _nh(p: Params, nz: int) -> int:
+    return nz if p.mode == PER_SLICE else 1
+
+
+def _levels(p: Params) -> int:
+    return (p.nbins >> p.shift) if p.two_d else p.nbins
+
+
+def _hist_shape(p: Params, nh: int):
+    L = _levels(p)
+    return (nh, L, L) if p.two_d else (nh, L)
+
+
+def tsallis_histogram(vol: torch.Tensor, p: Params | None = None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Step 1: int32 histograms [nh][L] (2-D: [nh][L2][L2])."""
+    p = p or tsallis_params()
+    nx, ny, nz = _vol3(vol)
+    nh = _nh(p, nz)
+    if out is None:
+        out = torch.empty(_hist_shape(p, nh), dtype=torch.int32, device=vol.device)
+    _check("tsallis_histogram", lib().tsallis_histogram(context(vol.device), vol.data_ptr(), nx, ny, nz,
+                                                        ctypes.byref(p), out.data_ptr(), _stream(vol)))
+    return out
+
+
+def tsallis_search(hist: torch.Tensor, p: Params | None = None, curve: bool = False):
+    """Steps 2-3: (t, phi, status[, curve]) for each histogram."""
+    p = p or tsallis_params()
+    if not hist.is_cuda or hist.dtype != torch.int32 or not hist.is_contiguous():
+        raise TypeError("hist must be a contiguous int32 CUDA tensor")
+    L = _levels(p)
+    per = L * L if p.two_d else L
+    if hist.numel() % per:
+        raise ValueError("histogram size does not match nbins")
+    nh = hist.numel() // per
+    dev = hist.device
+    t = torch.empty((nh, 2) if p.two_d else (nh,), dtype=torch.int32, device=dev)
+    phi = torch.empty(nh, dtype=torch.float32, device=dev)
+    st = torch.empty(nh, dtype=torch.int32, device=dev)
+    cv = None
+    if curve:
+        cv = torch.empty((nh, L - 1, L - 1) if p.two_d else (nh, L - 1), dtype=torch.float32, device=dev)
+    _check("tsallis_search", lib().tsallis_search(context(dev), hist.data_ptr(), nh, ctypes.byref(p), t.data_ptr(),
+                                                  phi.data_ptr(), st.data_ptr(),
+                                                  cv.data_ptr() if cv is not None else None, _stream(hist)))
+    return (t, phi, st, cv) if curve else (t, phi, st)
+
+
+def tsallis_binarize(vol: torch.Tensor, t: torch.Tensor, p: Params | None = None,
+                     out: torch.Tensor | None = None) -> torch.Tensor:
+    """Step 4 (Algorithm 1): uint8 mask with the thresholds in t."""
+    p = p or tsallis_params()
+    nx, ny, nz = _vol3(vol)
+    if not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
+        raise TypeError("t must be a contiguous int32 CUDA tensor")
+    if out is None:
+        out = torch.empty(vol.shape, dtype=torch.uint8, device=vol.device)
+    _check("tsallis_binarize", lib().tsallis_binarize(context(vol.device), vol.data_ptr(), nx, ny, nz, t.data_ptr(),
+                                                      ctypes.byref(p), out.data_ptr(), _stream(vol)))
+    return out
+
+
+def tsallis_segment(vol: torch.Tensor, p: Params | None = None, mask: torch.Tensor | None = None,
+                    t: torch.Tensor | None = None, phi: torch.Tensor | None = None,
+                    status: torch.Tensor | None = None):
+    """Steps 1-4 fused: (mask, t, phi, status)."""
+    p = p or tsallis_params()
+    nx, ny, nz = _vol3(vol)
+    nh = _nh(p, nz)
+    dev = vol.device
+    if mask is None:
+        mask = torch.empty(vol.shape, dtype=torch.uint8, device=dev)
+    if t is None:
+        t = torch.empty((nh, 2) if p.two_d else (nh,), dtype=torch.int32, device=dev)
+    if phi is None:
+        phi = torch.empty(nh, dtype=torch.float32, device=dev)
+    if status is None:
+        status = torch.empty(nh, dtype=torch.int32, device=dev)
+    _check("tsallis_segment", lib().tsallis_segment(context(dev), vol.data_ptr(), nx, ny, nz, ctypes.byref(p),
+                                                    mask.data_ptr(), t.data_ptr(), phi.data_ptr(),
+                                                    status.data_ptr(), _stream(vol)))
+    return mask, t, phi, status
+
+
+def tsallis_segment_batch(vols, p: Params | None = None, masks=None):
+    """Steps 1-4 for a list of volumes in one launch: (masks, t, phi, status)."""
+    p = p or tsallis_params()
+    vols = list(vols)
+    if not vols:
+        raise ValueError("empty batch")
+    dev = vols[0].device
+    if masks is None:
+        masks = [torch.empty(v.shape, dtype=torch.uint8, device=dev) for v in vols]
+    arr = (Volume * len(vols))()
+    nh = 0
+    for i, (v, m) in enumerate(zip(vols, masks)):
+        nx, ny, nz = _vol3(v)
+        arr[i] = Volume(v.data_ptr(), m.data_ptr(), nx, ny, nz)
+        nh += _nh(p, nz)
+    t = torch.empty((nh, 2) if p.two_d else (nh,), dtype=torch.int32, device=dev)
+    phi = torch.empty(nh, dtype=torch.float32, device=dev)
+    st = torch.empty(nh, dtype=torch.int32, device=dev)
+    _check("tsallis_segment_batch", lib().tsallis_segment_batch(context(dev), arr, len(vols), ctypes.byref(p),
+                                                                t.data_ptr(), phi.data_ptr(), st.data_ptr(),
+                                                                _stream(vols[0])))
+    return masks, t, phi, st

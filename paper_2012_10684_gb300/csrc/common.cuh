@@ -1,0 +1,204 @@
+// Device building blocks shared by the kernels of the thresholding path.
+//
+// Method: maximum Tsallis entropy threshold (section II-C "Segmentation",
+// "Tsallis entropy"), 1-D reading: for a threshold t, class 1 holds levels
+// 0..t and class 2 levels t+1..L-1. With counts h_i, N_1 = sum_{i<=t} h_i,
+// Q_1 = sum_{i<=t} h_i^q (and the same over i > t for class 2),
+//     sum_{i in class k} (p_i / P_k)^q = Q_k / N_k^q,
+// the normalisation p_i = h_i / N cancels, and the pseudo-additive objective
+//     phi = H_1 + H_2 + (1 - q) H_1 H_2,  H_k = (1 - Q_k / N_k^q) / (q - 1)
+// equals (1 - a b) / (q - 1) with a = Q_1 / N_1^q, b = Q_2 / N_2^q.
+// At q = 1 (Shannon limit) H_k = ln N_k - (sum h ln h) / N_k and phi = H_1 + H_2.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tsl {
+
+constexpr int kMaxBins = 4096;  // equals kMaxLevels of kernels.h
+
+// ------------------------------------------------------------ compensated FP32
+// A value held as an unevaluated sum hi + lo (Knuth's TwoSum error-free
+// transformation). All summands on this path are >= 0.
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+    F2 s = two_sum(x.hi, y.hi);
+    float lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    float hi = __fadd_rn(s.hi, lo);                 // renormalise (fast two-sum)
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+
+__device__ __forceinline__ F2 f2_add_f(F2 x, float y) { return f2_add(x, F2{y, 0.f}); }
+__device__ __forceinline__ float f2_val(F2 x) { return __fadd_rn(x.hi, x.lo); }
+
+__device__ __forceinline__ F2 shfl_up_f2(F2 v, int d) {
+    return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+}
+__device__ __forceinline__ F2 shfl_down_f2(F2 v, int d) {
+    return {__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+}
+
+// Inclusive warp scans.
+__device__ __forceinline__ long long warp_prefix_i64(long long v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        long long o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+__device__ __forceinline__ F2 warp_prefix_f2(F2 v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        F2 o = shfl_up_f2(v, d);
+        if (lane >= d) v = f2_add(o, v);
+    }
+    return v;
+}
+__device__ __forceinline__ F2 warp_suffix_f2(F2 v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        F2 o = shfl_down_f2(v, d);
+        if (lane + d < 32) v = f2_add(v, o);
+    }
+    return v;
+}
+__device__ __forceinline__ double warp_prefix_f64(double v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        double o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+__device__ __forceinline__ double warp_suffix_f64(double v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        double o = __shfl_down_sync(0xffffffffu, v, d);
+        if (lane + d < 32) v += o;
+    }
+    return v;
+}
+
+// (value, index) maximum; equal values keep the smaller index.
+template <typename T>
+__device__ __forceinline__ void argmax_merge(T& v, int& i, T ov, int oi) {
+    if (oi >= 0 && (i < 0 || ov > v || (ov == v && oi < i))) { v = ov; i = oi; }
+}
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T& v, int& i) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        T ov = __shfl_xor_sync(0xffffffffu, v, d);
+        int oi = __shfl_xor_sync(0xffffffffu, i, d);
+        argmax_merge(v, i, ov, oi);
+    }
+}
+
+// ------------------------------------------------------------ error band
+// Bound on |phi_fp32 - phi_exact| used to decide which thresholds may still
+// beat the FP32 maximiser. Derivation (CUDA documents powf to 4 ulp, logf to
+// 1 ulp, IEEE division and addition to 0.5 ulp; 1 ulp <= 2^-23 relative):
+//   Q_k (compensated sum of terms each within 4 ulp): 4 ulp + 0.5 ulp;
+//   N_k^q: 4 ulp + q * 0.5 ulp (int -> float rounding);
+//   a = Q/N^q: about 9 + q/2 ulp; ab: about 19 + q ulp = (2.3 + 0.12 q) e-6;
+//   phi = (1 - ab)/(q - 1) then errs by |ab| * that / |q - 1| plus 1 ulp of phi.
+// The constants below carry a further factor of two as margin.
+__device__ __forceinline__ float tsallis_err(float ab, float phi, float q) {
+    float rel = 4.6e-6f + 2.4e-7f * q;
+    return rel * fabsf(ab) / fabsf(q - 1.0f) + 2.4e-7f * fabsf(phi);
+}
+// Shannon limit: H_k = ln N_k - S_k / N_k with S_k a sum of h ln h (each
+// term within 2.5 ulp). Error <= 1 ulp of each log, 3.5 ulp of S/N, 1 ulp of
+// each H and of phi; doubled.
+__device__ __forceinline__ float shannon_err(float lna, float sa, float lnb, float sb, float phi) {
+    return 1.0e-6f * (fabsf(lna) + fabsf(sa) + fabsf(lnb) + fabsf(sb) + fabsf(phi) + 1.0f);
+}
+
+// ------------------------------------------------------------ 1-D search
+// One thread block searches one histogram of L <= 4096 levels.
+constexpr int kSearchThreads = 512;
+constexpr int kBinsPerThread = kMaxBins / kSearchThreads;  // 8
+constexpr int kSearchWarps = kSearchThreads / 32;
+
+struct SearchSmem {
+    long long cnt_pre[kSearchWarps];
+    F2 w_pre[kSearchWarps];
+    F2 w_suf[kSearchWarps];
+    double d_pre[kSearchWarps];
+    double d_suf[kSearchWarps];
+    float red_v[kSearchWarps];
+    int red_i[kSearchWarps];
+    double red_dv[kSearchWarps];
+    long long total;
+    float best_phi, best_err;
+    int best_t;
+    long long best_na;
+    int canon_t;
+};
+
+struct SearchResult {
+    int t;          // -1 when no threshold is valid
+    float phi;
+    int status;     // tsallis_status | extra bits
+};
+
+// h: the histogram in global memory (read through L2, so values written by
+// atomics of other blocks are seen). curve: optional [L-1] output.
+__device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, float q, float* __restrict__ curve,
+                                       SearchSmem& sm);
+
+// ------------------------------------------------------------ streaming tiles
+
+__device__ __forceinline__ int level_of(int v, int lo, int L) {
+    int b = v - lo;
+    b = b < 0 ? 0 : b;
+    return b > L - 1 ? L - 1 : b;
+}
+
+__device__ __forceinline__ uint4 ld_stream_keep(const void* p) {
+    // read-only path, no L1 allocation; the line stays in L2 for the re-read
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint4 ld_last_use(const void* p) {
+    // last use of the line: evict-first in L2
+    uint4 r;
+    asm volatile("ld.global.cs.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ void st_stream(void* p, uint2 v) {
+    asm volatile("st.global.cs.v2.u32 [%0], {%1,%2};" ::"l"(p), "r"(v.x), "r"(v.y) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace tsl
