@@ -45,7 +45,7 @@ extern "C" {
 
 typedef enum {
     TSALLIS_OK = 0,
-    TSALLIS_ERR_INVALID_ARG = 1,       /* null pointer, bad size, q <= 0 or not finite, ... */
+    TSALLIS_ERR_INVALID_ARG = 1,       /* null pointer, bad size, q outside (0, 4], ... */
     TSALLIS_ERR_ALIGNMENT = 2,         /* a volume or mask pointer is not 16-byte aligned */
     TSALLIS_ERR_CUDA = 3,              /* a CUDA runtime call failed */
     TSALLIS_ERR_NO_VALID_THRESHOLD = 4,/* per histogram: fewer than two non-empty levels */
@@ -72,10 +72,10 @@ typedef enum {
                                                 arrival, so waits on its histogram run out */
 
 typedef struct {
-    int32_t lo;       /* Hounsfield value of level 0; default -1024 */
+    int32_t lo;       /* Hounsfield value of level 0, -32768..32767; default -1024 */
     int32_t nbins;    /* L, number of 1-D levels, 2..4096; default 4096. Level of a
                          voxel v is b = clamp(v - lo, 0, L - 1). */
-    float q;          /* Tsallis index (alpha), > 0 and finite; q == 1 selects the
+    float q;          /* Tsallis index (alpha), 0 < q <= 4; q == 1 selects the
                          Shannon (Kapur) limit. Default 0.8 */
     int32_t mode;     /* tsallis_mode; default TSALLIS_PER_SLICE */
     int32_t polarity; /* tsallis_polarity; default TSALLIS_MASK_LOW */
@@ -95,7 +95,8 @@ tsallis_status tsallis_params_default(tsallis_params* p);
 const char* tsallis_status_string(int32_t status);
 
 /* Creates a context bound to CUDA device `device`. *ctx receives the handle.
- * Allocates nothing on the device until the first call that needs scratch. */
+ * Allocates a few kilobytes of constant tables on the device; scratch for
+ * the kernels is allocated by the first call that needs it. */
 tsallis_status tsallis_create(tsallis_ctx** ctx, int device);
 
 /* Releases the context's scratch memory. Safe with NULL. The caller must
@@ -105,6 +106,14 @@ void tsallis_destroy(tsallis_ctx* ctx);
 /* Limit, in nanoseconds, on every device-side wait of this context
  * (default 1e9). A wait that runs out writes TSALLIS_ERR_TIMEOUT. */
 tsallis_status tsallis_set_wait_timeout(tsallis_ctx* ctx, uint64_t ns);
+
+/*
+ * Launch shape of the persistent kernels (the counterpart of the grid/block
+ * tuning in the paper's Table 4): voxels per work tile (a multiple of 8 in
+ * 4096..2^22; default 65536) and resident blocks per SM used for the grid
+ * (0 = as many as fit). Returns TSALLIS_ERR_INVALID_ARG outside those ranges.
+ */
+tsallis_status tsallis_set_launch_shape(tsallis_ctx* ctx, int32_t tile_vox, int32_t blocks_per_sm);
 
 /*
  * Step 1: histogram (section I "Thresholding", Fig. 2; 2-D: section II-C,

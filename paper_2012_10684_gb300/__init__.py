@@ -74,12 +74,14 @@ _SIGS = {
     "tsallis_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int], ctypes.c_int),
     "tsallis_destroy": ([_P], None),
     "tsallis_set_wait_timeout": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "tsallis_set_launch_shape": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "tsallis_histogram": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(Params), _P, _P], ctypes.c_int),
     "tsallis_search": ([_P, _P, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
     "tsallis_binarize": ([_P, _P, _I64, _I64, _I64, _P, ctypes.POINTER(Params), _P, _P], ctypes.c_int),
     "tsallis_segment": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
     "tsallis_segment_batch": ([_P, ctypes.POINTER(Volume), ctypes.c_int32, ctypes.POINTER(Params), _P, _P, _P, _P],
                               ctypes.c_int),
+    "tsallis_probe_dfmath": ([_P, _P, _I64, ctypes.c_uint32, ctypes.c_float, _P, _P, _P], ctypes.c_int),
 }
 
 
@@ -134,6 +136,23 @@ def context(device=None) -> int:
 
 def set_wait_timeout(ns: int, device=None) -> None:
     _check("tsallis_set_wait_timeout", lib().tsallis_set_wait_timeout(context(device), int(ns)))
+
+
+def set_launch_shape(tile_vox: int = 32768, blocks_per_sm: int = 0, device=None) -> None:
+    """Launch shape of the persistent kernels (see tsallis_set_launch_shape)."""
+    _check("tsallis_set_launch_shape",
+           lib().tsallis_set_launch_shape(context(device), int(tile_vox), int(blocks_per_sm)))
+
+
+def tsallis_probe_dfmath(h: torch.Tensor, N: int, q: float):
+    """Test hook: ((h/N)^q, log2 h) as computed by the search's double-float math."""
+    if not h.is_cuda or h.dtype != torch.int32 or not h.is_contiguous():
+        raise TypeError("h must be a contiguous int32 CUDA tensor of counts")
+    pw = torch.empty(h.numel(), dtype=torch.float64, device=h.device)
+    lg = torch.empty(h.numel(), dtype=torch.float64, device=h.device)
+    _check("tsallis_probe_dfmath", lib().tsallis_probe_dfmath(context(h.device), h.data_ptr(), h.numel(), int(N),
+                                                              float(q), pw.data_ptr(), lg.data_ptr(), _stream(h)))
+    return pw, lg
 
 
 def tsallis_params(q: float = 0.8, lo: int = -1024, nbins: int = 4096, mode="slice", polarity="low",

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/tsallis.h"
+#include "../../include/tsallis_testing.h"
 #include "kernels.h"
 
 using namespace tsl;
@@ -18,14 +19,18 @@ struct tsallis_ctx {
     void* scratch = nullptr;      // ScratchHeader, then per-group arrays
     size_t scratch_bytes = 0;
     long long cap_groups = 0;
+    long long cap_tiles = 0;
     unsigned long long timeout_ns = 1000000000ull;
     // launch shape of the 1-D persistent kernel
     int copies = 1;
-    int tile_vox = 32768;
-    int blocks_per_sm = 0;
+    int tile_vox = 65536;
+    int blocks_per_sm = 0;        // resident blocks per SM used for the grid
+    int max_blocks_per_sm = 0;    // what the occupancy calculator allows
     // batch work list (device copy) and its host image
     void* batch_buf = nullptr;
     size_t batch_bytes = 0;
+    void* df_tables = nullptr;    // double-float log2/exp2 tables (device)
+    void* log2_table = nullptr;   // log2 of counts up to 2^18 as float pairs (device)
 };
 
 namespace {
@@ -51,9 +56,9 @@ class DeviceGuard {
 
 tsallis_status check_params(const tsallis_params* p) {
     if (!p) return TSALLIS_ERR_INVALID_ARG;
-    if (!(p->q > 0.0f) || !std::isfinite(p->q)) return TSALLIS_ERR_INVALID_ARG;
+    if (!(p->q > 0.0f) || !(p->q <= 4.0f)) return TSALLIS_ERR_INVALID_ARG;
     if (p->nbins < 2 || p->nbins > kMaxLevels) return TSALLIS_ERR_INVALID_ARG;
-    if (p->lo < -65536 || p->lo > 65535) return TSALLIS_ERR_INVALID_ARG;
+    if (p->lo < -32768 || p->lo > 32767) return TSALLIS_ERR_INVALID_ARG;
     if (p->mode != TSALLIS_PER_SLICE && p->mode != TSALLIS_WHOLE_VOLUME) return TSALLIS_ERR_INVALID_ARG;
     if (p->polarity != TSALLIS_MASK_LOW && p->polarity != TSALLIS_MASK_HIGH) return TSALLIS_ERR_INVALID_ARG;
     if (p->two_d != 0 && p->two_d != 1) return TSALLIS_ERR_INVALID_ARG;
@@ -76,63 +81,73 @@ tsallis_status check_shape(int64_t nx, int64_t ny, int64_t nz) {
     return TSALLIS_OK;
 }
 
-// Grows the context's scratch so it holds at least ngroups groups. The
-// layout depends only on the capacity (arrive[cap], ready[cap], tmo[cap], then
-// ghist[cap][kMaxLevels]), so state left by one launch lines up with the next.
-// New memory is zeroed; the kernels keep it zeroed between launches.
-size_t scratch_layout(long long cap, size_t* ghist_off) {
-    size_t off = sizeof(ScratchHeader) + (size_t)cap * 3 * sizeof(int);
+// Grows the context's scratch so it holds at least ngroups groups and
+// ntiles work tiles. The layout depends only on the capacities (arrive,
+// done_flag, bdone [capg]; ghist [capg][kMaxLevels]; bq [capt]), so state
+// left by one launch lines up with the next. New memory is zeroed; the
+// kernels keep it consistent between launches.
+size_t scratch_layout(long long capg, long long capt, size_t* ghist_off, size_t* bq_off) {
+    size_t off = sizeof(ScratchHeader) + (size_t)capg * 3 * sizeof(int);
     off = (off + 255) & ~size_t(255);
     if (ghist_off) *ghist_off = off;
-    return off + (size_t)cap * kMaxLevels * sizeof(int);
+    off += (size_t)capg * kMaxLevels * sizeof(int);
+    off = (off + 255) & ~size_t(255);
+    if (bq_off) *bq_off = off;
+    return off + (size_t)capt * sizeof(unsigned long long);
 }
 
-tsallis_status ensure_scratch(tsallis_ctx* c, long long ngroups) {
-    if (c->scratch && ngroups <= c->cap_groups) return TSALLIS_OK;
-    long long cap = c->cap_groups > 0 ? c->cap_groups : 16;
-    while (cap < ngroups) cap *= 2;
+tsallis_status ensure_scratch(tsallis_ctx* c, long long ngroups, long long ntiles) {
+    if (c->scratch && ngroups <= c->cap_groups && ntiles <= c->cap_tiles) return TSALLIS_OK;
+    long long capg = c->cap_groups > 0 ? c->cap_groups : 16;
+    long long capt = c->cap_tiles > 0 ? c->cap_tiles : 4096;
+    while (capg < ngroups) capg *= 2;
+    while (capt < ntiles) capt *= 2;
     if (c->scratch) {
         if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
         cudaFree(c->scratch);
         c->scratch = nullptr;
         c->scratch_bytes = 0;
         c->cap_groups = 0;
+        c->cap_tiles = 0;
     }
-    const size_t bytes = scratch_layout(cap, nullptr);
+    const size_t bytes = scratch_layout(capg, capt, nullptr, nullptr);
     if (cudaMalloc(&c->scratch, bytes) != cudaSuccess) {
         cudaGetLastError();
         return TSALLIS_ERR_OOM;
     }
     if (cudaMemset(c->scratch, 0, bytes) != cudaSuccess) return TSALLIS_ERR_CUDA;
     c->scratch_bytes = bytes;
-    c->cap_groups = cap;
+    c->cap_groups = capg;
+    c->cap_tiles = capt;
     return TSALLIS_OK;
 }
 
 struct ScratchView {
     ScratchHeader* hdr;
     int* arrive;
-    int* ready;
-    int* tmo;
+    int* done_flag;
+    int* bdone;
     int* ghist;
+    unsigned long long* bq;
 };
 
 ScratchView view(tsallis_ctx* c) {
     char* b = (char*)c->scratch;
-    size_t goff = 0;
-    scratch_layout(c->cap_groups, &goff);
+    size_t goff = 0, qoff = 0;
+    scratch_layout(c->cap_groups, c->cap_tiles, &goff, &qoff);
     ScratchView v;
     v.hdr = (ScratchHeader*)b;
     v.arrive = (int*)(b + sizeof(ScratchHeader));
-    v.ready = v.arrive + c->cap_groups;
-    v.tmo = v.ready + c->cap_groups;
+    v.done_flag = v.arrive + c->cap_groups;
+    v.bdone = v.done_flag + c->cap_groups;
     v.ghist = (int*)(b + goff);
+    v.bq = (unsigned long long*)(b + qoff);
     return v;
 }
 
-int grid_for(tsallis_ctx* c, unsigned nticket) {
+int grid_for(tsallis_ctx* c, unsigned nitems) {
     long long g = (long long)c->sm_count * (c->blocks_per_sm > 0 ? c->blocks_per_sm : 1);
-    if ((long long)nticket < g) g = nticket;
+    if ((long long)nitems < g) g = nitems;
     return (int)(g < 1 ? 1 : g);
 }
 
@@ -146,6 +161,7 @@ void fill_common(SegArgs& a, const tsallis_params* p, tsallis_ctx* c) {
     a.flags = p->flags;
     a.timeout_ns = c->timeout_ns;
     a.tile_vox = c->tile_vox;
+    a.df_tables = c->df_tables;
 }
 
 tsallis_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TSALLIS_OK : TSALLIS_ERR_CUDA; }
@@ -201,7 +217,33 @@ tsallis_status tsallis_create(tsallis_ctx** out, int device) {
         return TSALLIS_ERR_CUDA;
     }
     c->l2_bytes = l2;
-    if (segment1d_occupancy(c->copies, kMaxLevels, &c->blocks_per_sm) != cudaSuccess || c->blocks_per_sm < 1) {
+    if (segment1d_prepare() != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return TSALLIS_ERR_CUDA;
+    }
+    if (segment1d_occupancy(c->copies, kMaxLevels, &c->max_blocks_per_sm) != cudaSuccess ||
+        c->max_blocks_per_sm < 1) {
+        delete c;
+        return TSALLIS_ERR_CUDA;
+    }
+    c->blocks_per_sm = c->max_blocks_per_sm;
+    // double-float tables: the small reduction tables (host-built), then a
+    // log2 table of counts up to 2^18 computed on the device from them
+    std::vector<unsigned char> tab(df_tables_bytes());
+    if (cudaMalloc(&c->log2_table, sizeof(float) * 2 * (size_t)(kLog2TableMax + 1)) != cudaSuccess ||
+        cudaMalloc(&c->df_tables, tab.size()) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->log2_table) cudaFree(c->log2_table);
+        delete c;
+        return TSALLIS_ERR_OOM;
+    }
+    df_tables_fill(tab.data(), c->log2_table, kLog2TableMax);
+    if (cudaMemcpy(c->df_tables, tab.data(), tab.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        build_log2_table(c->log2_table, kLog2TableMax + 1, c->df_tables, 0) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(c->df_tables);
+        cudaFree(c->log2_table);
         delete c;
         return TSALLIS_ERR_CUDA;
     }
@@ -215,6 +257,8 @@ void tsallis_destroy(tsallis_ctx* c) {
         DeviceGuard g(c->device);
         if (c->scratch) cudaFree(c->scratch);
         if (c->batch_buf) cudaFree(c->batch_buf);
+        if (c->df_tables) cudaFree(c->df_tables);
+        if (c->log2_table) cudaFree(c->log2_table);
     }
     delete c;
 }
@@ -222,6 +266,15 @@ void tsallis_destroy(tsallis_ctx* c) {
 tsallis_status tsallis_set_wait_timeout(tsallis_ctx* c, uint64_t ns) {
     if (!c || ns == 0) return TSALLIS_ERR_INVALID_ARG;
     c->timeout_ns = ns;
+    return TSALLIS_OK;
+}
+
+tsallis_status tsallis_set_launch_shape(tsallis_ctx* c, int32_t tile_vox, int32_t blocks_per_sm) {
+    if (!c) return TSALLIS_ERR_INVALID_ARG;
+    if (tile_vox < 4096 || tile_vox > (1 << 22) || (tile_vox & 7)) return TSALLIS_ERR_INVALID_ARG;
+    if (blocks_per_sm < 0 || blocks_per_sm > c->max_blocks_per_sm) return TSALLIS_ERR_INVALID_ARG;
+    c->tile_vox = tile_vox;
+    c->blocks_per_sm = blocks_per_sm > 0 ? blocks_per_sm : c->max_blocks_per_sm;
     return TSALLIS_OK;
 }
 
@@ -241,7 +294,7 @@ tsallis_status tsallis_histogram(tsallis_ctx* c, const int16_t* d_vol, int64_t n
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
-    if ((st = ensure_scratch(c, 0)) != TSALLIS_OK) return st;
+    if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
     if (cudaMemsetAsync(d_hist, 0, (size_t)ng * p->nbins * sizeof(int32_t), stream) != cudaSuccess)
         return TSALLIS_ERR_CUDA;
     SegArgs a;
@@ -251,11 +304,12 @@ tsallis_status tsallis_histogram(tsallis_ctx* c, const int16_t* d_vol, int64_t n
     a.ngroups = (int)ng;
     a.ntiles = (int)((gvox + a.tile_vox - 1) / a.tile_vox);
     a.phases = kPhaseHist;
-    a.nticket = (unsigned)(ng * a.ntiles);
+    if (ng * a.ntiles > 0xffffffffll) return TSALLIS_ERR_INVALID_ARG;
+    a.ntotal = (unsigned)(ng * a.ntiles);
     ScratchView v = view(c);
     a.hdr = v.hdr;
     a.ghist = d_hist;
-    return cuda_status(launch_segment1d(a, grid_for(c, a.nticket), c->copies, stream));
+    return cuda_status(launch_segment1d(a, grid_for(c, a.ntotal), c->copies, stream));
 }
 
 tsallis_status tsallis_search(tsallis_ctx* c, const int32_t* d_hist, int64_t nh, const tsallis_params* p,
@@ -269,7 +323,8 @@ tsallis_status tsallis_search(tsallis_ctx* c, const int32_t* d_hist, int64_t nh,
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
-    return cuda_status(launch_search1d(d_hist, nh, p->nbins, p->q, d_t, d_phi, d_status, d_curve, stream));
+    return cuda_status(launch_search1d(d_hist, nh, p->nbins, p->q, d_t, d_phi, d_status, d_curve, c->df_tables,
+                                       stream));
 }
 
 tsallis_status tsallis_binarize(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
@@ -288,7 +343,7 @@ tsallis_status tsallis_binarize(tsallis_ctx* c, const int16_t* d_vol, int64_t nx
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
-    if ((st = ensure_scratch(c, 0)) != TSALLIS_OK) return st;
+    if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
     SegArgs a;
     fill_common(a, p, c);
     a.vol = d_vol;
@@ -297,11 +352,12 @@ tsallis_status tsallis_binarize(tsallis_ctx* c, const int16_t* d_vol, int64_t nx
     a.ngroups = (int)ng;
     a.ntiles = (int)((gvox + a.tile_vox - 1) / a.tile_vox);
     a.phases = kPhaseBin;
-    a.nticket = (unsigned)(ng * a.ntiles);
+    if (ng * a.ntiles > 0xffffffffll) return TSALLIS_ERR_INVALID_ARG;
+    a.ntotal = (unsigned)(ng * a.ntiles);
     a.t_in = d_t;
     ScratchView v = view(c);
     a.hdr = v.hdr;
-    return cuda_status(launch_segment1d(a, grid_for(c, a.nticket), c->copies, stream));
+    return cuda_status(launch_segment1d(a, grid_for(c, a.ntotal), c->copies, stream));
 }
 
 tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
@@ -321,7 +377,7 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
-    if ((st = ensure_scratch(c, ng)) != TSALLIS_OK) return st;
+    if ((st = ensure_scratch(c, ng, ng * ((gvox + c->tile_vox - 1) / c->tile_vox))) != TSALLIS_OK) return st;
     SegArgs a;
     fill_common(a, p, c);
     a.vol = d_vol;
@@ -330,24 +386,29 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
     a.ngroups = (int)ng;
     a.ntiles = (int)((gvox + a.tile_vox - 1) / a.tile_vox);
     a.phases = kPhaseHist | kPhaseSearch | kPhaseBin;
-    const int grid0 = grid_for(c, 0xffffffffu);
-    // binarise items trail histogram items by enough steps to cover the
-    // items in flight, so their waits are normally already satisfied
-    const int steps_in_flight = (grid0 + 2 * a.ntiles - 1) / (2 * a.ntiles);
-    a.lag = ng == 1 ? 1 : steps_in_flight + 4;
-    const long long nt = (ng + a.lag) * 2ll * a.ntiles;
-    if (nt > 0xffffffffll) return TSALLIS_ERR_INVALID_ARG;
-    a.nticket = (unsigned)nt;
+    if (ng * a.ntiles > 0xffffffffll) return TSALLIS_ERR_INVALID_ARG;
+    a.ntotal = (unsigned)(ng * a.ntiles);
     ScratchView v = view(c);
     a.hdr = v.hdr;
     a.arrive = v.arrive;
-    a.ready = v.ready;
-    a.tmo = v.tmo;
+    a.done_flag = v.done_flag;
+    a.bdone = v.bdone;
+    a.bq = v.bq;
     a.ghist = v.ghist;
     a.t_out = d_t;
     a.phi_out = d_phi;
     a.status = d_status;
-    return cuda_status(launch_segment1d(a, grid_for(c, a.nticket), c->copies, stream));
+    return cuda_status(launch_segment1d(a, grid_for(c, a.ntotal), c->copies, stream));
+}
+
+tsallis_status tsallis_probe_dfmath(tsallis_ctx* c, const uint32_t* d_h, int64_t n, uint32_t N, float q,
+                                   double* d_pow, double* d_log2, cudaStream_t stream) {
+    if (!c || n < 0 || N < 1 || !(q > 0.0f) || !(q <= 4.0f)) return TSALLIS_ERR_INVALID_ARG;
+    if (n == 0) return TSALLIS_OK;
+    if (!d_h || !d_pow || !d_log2) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    return cuda_status(launch_probe_dfmath(d_h, n, N, q, d_pow, d_log2, c->df_tables, stream));
 }
 
 tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vols, int32_t nvol,

@@ -107,22 +107,23 @@ __device__ __forceinline__ void warp_argmax(T& v, int& i) {
 
 // ------------------------------------------------------------ error band
 // Bound on |phi_fp32 - phi_exact| used to decide which thresholds may still
-// beat the FP32 maximiser. Derivation (CUDA documents powf to 4 ulp, logf to
-// 1 ulp, IEEE division and addition to 0.5 ulp; 1 ulp <= 2^-23 relative):
-//   Q_k (compensated sum of terms each within 4 ulp): 4 ulp + 0.5 ulp;
-//   N_k^q: 4 ulp + q * 0.5 ulp (int -> float rounding);
-//   a = Q/N^q: about 9 + q/2 ulp; ab: about 19 + q ulp = (2.3 + 0.12 q) e-6;
-//   phi = (1 - ab)/(q - 1) then errs by |ab| * that / |q - 1| plus 1 ulp of phi.
+// beat the FP32 maximiser. The class sums come from double-float sums, so
+// rounding them to float costs 0.5 ulp each; the class powers (N_k/N)^q use
+// powf, which CUDA documents to 4 ulp, on a ratio carrying 1.5 ulp (two
+// int->float roundings and a division), i.e. 4 + 1.5 q ulp; the two
+// divisions and the product add 0.5 ulp each. So ab is within
+// (10.5 + 3 q) ulp, 1 ulp <= 2^-23 relative, and
+//     |dphi| <= |ab| * (10.5 + 3 q) 2^-23 / |q - 1| + 1 ulp of phi.
 // The constants below carry a further factor of two as margin.
 __device__ __forceinline__ float tsallis_err(float ab, float phi, float q) {
-    float rel = 4.6e-6f + 2.4e-7f * q;
+    float rel = 2.51e-6f + 7.16e-7f * q;
     return rel * fabsf(ab) / fabsf(q - 1.0f) + 2.4e-7f * fabsf(phi);
 }
-// Shannon limit: H_k = ln N_k - S_k / N_k with S_k a sum of h ln h (each
-// term within 2.5 ulp). Error <= 1 ulp of each log, 3.5 ulp of S/N, 1 ulp of
-// each H and of phi; doubled.
-__device__ __forceinline__ float shannon_err(float lna, float sa, float lnb, float sb, float phi) {
-    return 1.0e-6f * (fabsf(lna) + fabsf(sa) + fabsf(lnb) + fabsf(sb) + fabsf(phi) + 1.0f);
+// Shannon limit, in bits: H_k / ln 2 = log2 N_k - S_k / N_k. log2f is within
+// 1 ulp, S_k / N_k within 1.5 ulp, each subtraction and the final scaling
+// within 0.5 ulp; the bound below is several times that.
+__device__ __forceinline__ float shannon_err(float la, float sa, float lb, float sb, float phi_bits) {
+    return 1.0e-6f * (fabsf(la) + fabsf(sa) + fabsf(lb) + fabsf(sb) + fabsf(phi_bits) + 1.0f);
 }
 
 // ------------------------------------------------------------ 1-D search
@@ -145,6 +146,7 @@ struct SearchSmem {
     int best_t;
     long long best_na;
     int canon_t;
+    int flag;
 };
 
 struct SearchResult {
@@ -153,10 +155,6 @@ struct SearchResult {
     int status;     // tsallis_status | extra bits
 };
 
-// h: the histogram in global memory (read through L2, so values written by
-// atomics of other blocks are seen). curve: optional [L-1] output.
-__device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, float q, float* __restrict__ curve,
-                                       SearchSmem& sm);
 
 // ------------------------------------------------------------ streaming tiles
 

@@ -14,28 +14,25 @@ constexpr int kMaxLevels = 4096;  // largest 1-D histogram
 // to finish resets the ticket and done counters and bumps the epoch), so no
 // memset is needed between launches and CUDA-graph replays are safe.
 struct ScratchHeader {
-    unsigned int ticket;  // next work item
+    unsigned int h_next;  // next histogram work item
+    unsigned int b_next;  // next binarise queue position to claim
+    unsigned int b_tail;  // binarise queue positions reserved by published groups
     unsigned int done;    // blocks that have finished
-    int epoch;            // launches so far; ready flags are compared to epoch + 1
+    int epoch;            // launches so far; flags are compared to epoch + 1
     int err;              // a device wait ran out or an arrival was skipped
-    int pad[12];
+    int pad[9];
 };
 
 enum Phase : int { kPhaseHist = 1, kPhaseSearch = 2, kPhaseBin = 4 };
 
-// One work item of a batch: a histogram group and a tile of it.
-struct WorkItem {
-    int group;  // histogram group
-    int tile;   // tile index within the group; bit 31 set for a binarise tile
-};
-
-// A group (one histogram): voxel range and where its mask goes.
+// A group (one histogram) of a batch: its voxels, its mask, and where its
+// tiles start in the batch's sequence of histogram work items.
 struct GroupDesc {
     const int16_t* vol;
     uint8_t* mask;
     long long nvox;
     int ntiles;
-    int pad;
+    int tile_off;
 };
 
 struct SegArgs {
@@ -45,10 +42,8 @@ struct SegArgs {
     int ngroups;
     int ntiles;             // tiles per group (uniform groups)
     int tile_vox;           // voxels per tile, multiple of 8
-    int lag;                // binarise tiles of group s - lag follow histogram tiles of group s
-    unsigned int nticket;   // number of work items
-    const GroupDesc* groups;   // non-null: batch with an explicit work list
-    const WorkItem* worklist;
+    unsigned int ntotal;    // histogram (or binarise) work items in total
+    const GroupDesc* groups;   // non-null: batch of uneven groups
     int lo, L;
     float q;
     int polarity;
@@ -57,23 +52,34 @@ struct SegArgs {
     unsigned int flags;
     unsigned long long timeout_ns;
     ScratchHeader* hdr;
-    int* arrive;            // [ngroups]
-    int* ready;             // [ngroups]
-    int* tmo;               // [ngroups]: epoch + 1 when a wait on the group ran out
+    int* arrive;            // [ngroups] histogram tiles added so far
+    int* done_flag;         // [ngroups] epoch + 1 once the threshold is published
+    int* bdone;             // [ngroups] binarise tiles finished
+    unsigned long long* bq; // [ntotal] binarise queue (launch tag | group | tile)
     int* ghist;             // [ngroups][L]: histogram target (scratch or caller's)
     const int* t_in;        // binarise-only: caller's thresholds
     int* t_out;
     float* phi_out;
     int* status;
     float* curve;           // optional [ngroups][L-1]
+    const void* df_tables;  // double-float log2/exp2 tables (device)
 };
 
 // Kernel launchers (seg1d.cu).
 cudaError_t launch_segment1d(const SegArgs& a, int grid, int copies, cudaStream_t s);
 cudaError_t launch_search1d(const int32_t* hist, long long nh, int L, float q, int32_t* t, float* phi,
-                            int32_t* status, float* curve, cudaStream_t s);
+                            int32_t* status, float* curve, const void* tables, cudaStream_t s);
+cudaError_t launch_probe_dfmath(const unsigned* h, long long n, unsigned N, float q, double* pw, double* lg,
+                                const void* tables, cudaStream_t s);
+size_t df_tables_bytes();
+// log2_table: device array of (log2_table_max + 1) float2 entries, filled by
+// build_log2_table once the tables themselves are on the device.
+void df_tables_fill(void* host, const void* log2_table, int log2_table_max);
+cudaError_t build_log2_table(void* lt, int n, const void* tables, cudaStream_t s);
+constexpr int kLog2TableMax = 1 << 18;
 int segment1d_threads();
 int segment1d_smem_bytes(int L, int copies);
 cudaError_t segment1d_occupancy(int copies, int L, int* blocks_per_sm);
+cudaError_t segment1d_prepare();
 
 }  // namespace tsl

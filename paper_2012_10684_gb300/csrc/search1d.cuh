@@ -1,123 +1,219 @@
 // 1-D exhaustive threshold search, one thread block per histogram.
 //
-// Section II-C ("Tsallis entropy"), 1-D reading. Steps, all inside the block:
-//   1. each thread owns 8 consecutive levels; h^q (or h ln h at q = 1) in
-//      FP32, exact int64 counts;
-//   2. block-wide exclusive prefix scan of counts and of the compensated
-//      (hi, lo) sums of h^q, and a separate suffix scan for class 2 (class-2
-//      sums are never formed as total minus class-1 sums);
-//   3. phi(t) for every valid t with its error bound, block argmax with the
-//      smallest t among equal values;
-//   4. if any threshold giving a different partition lies within the error
-//      bands of the maximum, recompute phi for all of those candidates in
-//      FP64 (FP64 h^q, FP64 scans) and take their argmax;
-//   5. canonical t: the smallest t giving the same class-1 count (empty
-//      levels between classes do not change the partition).
+// Section II-C ("Tsallis entropy"), 1-D reading. With N the total count,
+// every term is scaled by N^-q (and by the constant 2^64 of dfmath.cuh,
+// which cancels in every ratio):
+//     w_i = (h_i / N)^q,  Q_1(t) = sum_{i<=t} w_i,  Q_2(t) = sum_{i>t} w_i,
+//     a = Q_1 / (N_1/N)^q,  b = Q_2 / (N_2/N)^q,  phi = (1 - a b) / (q - 1),
+// which is H_1 + H_2 + (1 - q) H_1 H_2 with H_k = (1 - sum (p_i/P_k)^q)/(q-1).
+// At q = 1 (Shannon limit) w_i = h_i log2 h_i and
+//     phi = ln 2 * [(log2 N_1 - Q_1/N_1) + (log2 N_2 - Q_2/N_2)].
+//
+// Steps, all inside the block (512 threads):
+//   1. compaction of the non-empty levels (see search1d_block), exact int64
+//      prefix sums of their counts (gives N and N_1);
+//   2. terms w_i as double-float pairs (dfmath.cuh), kept in shared memory;
+//      double-float prefix and suffix scans (class-2 sums are summed from
+//      the right, never formed as total minus class-1 sums);
+//   3. phi(t) in FP32 from the rounded sums, with a rigorous error bound,
+//      and the block argmax (smallest t among equal values);
+//   4. every threshold with a different partition whose FP32 value lies
+//      within the error bands of the maximum is a candidate; if there is
+//      one, all candidates are re-evaluated in FP64 from the double-float
+//      sums (class powers (N_k/N)^q also in double-float), and the FP64
+//      argmax wins;
+//   5. canonical t: the smallest t with the winning partition, which is the
+//      non-empty level the winning entry stands for.
 #pragma once
 #include "common.cuh"
+#include "dfmath.cuh"
 #include "../../include/tsallis.h"
 
 namespace tsl {
 
-__device__ __forceinline__ float term_f32(int h, float q, bool shannon) {
-    if (h <= 0) return 0.f;
-    float x = (float)h;
-    return shannon ? x * logf(x) : powf(x, q);
-}
-__device__ __forceinline__ double term_f64(int h, double q, bool shannon) {
-    if (h <= 0) return 0.0;
-    double x = (double)h;
-    return shannon ? x * log(x) : pow(x, q);
+// The 512 threads that run a search synchronise through a barrier policy:
+// the whole block (standalone search kernel) or a named barrier shared only
+// by the search warps of the fused kernel.
+struct BlockSync {
+    __device__ static void sync() { __syncthreads(); }
+    __device__ static int tid() { return threadIdx.x; }
+};
+template <int kBarrier, int kFirstThread>
+struct NamedSync {
+    __device__ static void sync() { asm volatile("bar.sync %0, %1;" ::"n"(kBarrier), "n"(kSearchThreads) : "memory"); }
+    __device__ static int tid() { return (int)threadIdx.x - kFirstThread; }
+};
+
+// Block-wide OR of a predicate through shared memory.
+template <class Sync>
+__device__ __forceinline__ bool block_any(bool p, SearchSmem& sm) {
+    if (Sync::tid() == 0) sm.flag = 0;
+    Sync::sync();
+    if (p) sm.flag = 1;
+    Sync::sync();
+    const bool r = sm.flag != 0;
+    Sync::sync();
+    return r;
 }
 
 // Block argmax over (value, index) pairs held one per thread; result in
 // sm.red_v[0] / sm.red_i[0] after the call (all threads synchronised).
+template <class Sync>
 __device__ __forceinline__ void block_argmax_f(float v, int i, SearchSmem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = Sync::tid() & 31, warp = Sync::tid() >> 5;
     warp_argmax(v, i);
     if (lane == 0) { sm.red_v[warp] = v; sm.red_i[warp] = i; }
-    __syncthreads();
+    Sync::sync();
     if (warp == 0) {
         v = lane < kSearchWarps ? sm.red_v[lane] : 0.f;
         i = lane < kSearchWarps ? sm.red_i[lane] : -1;
         warp_argmax(v, i);
         if (lane == 0) { sm.red_v[0] = v; sm.red_i[0] = i; }
     }
-    __syncthreads();
+    Sync::sync();
 }
+template <class Sync>
 __device__ __forceinline__ void block_argmax_d(double v, int i, SearchSmem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = Sync::tid() & 31, warp = Sync::tid() >> 5;
     warp_argmax(v, i);
     if (lane == 0) { sm.red_dv[warp] = v; sm.red_i[warp] = i; }
-    __syncthreads();
+    Sync::sync();
     if (warp == 0) {
         v = lane < kSearchWarps ? sm.red_dv[lane] : 0.0;
         i = lane < kSearchWarps ? sm.red_i[lane] : -1;
         warp_argmax(v, i);
         if (lane == 0) { sm.red_dv[0] = v; sm.red_i[0] = i; }
     }
-    __syncthreads();
+    Sync::sync();
 }
+template <class Sync>
 __device__ __forceinline__ int block_min_i(int v, SearchSmem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = Sync::tid() & 31, warp = Sync::tid() >> 5;
     v = __reduce_min_sync(0xffffffffu, v);
     if (lane == 0) sm.red_i[warp] = v;
-    __syncthreads();
+    Sync::sync();
     if (warp == 0) {
         v = lane < kSearchWarps ? sm.red_i[lane] : 0x7fffffff;
         v = __reduce_min_sync(0xffffffffu, v);
         if (lane == 0) sm.canon_t = v;
     }
-    __syncthreads();
+    Sync::sync();
     return sm.canon_t;
 }
 
+// Scratch (shared memory): sT[kMaxBins] float2 and sIC[kMaxBins] int2.
+//
+// Only non-empty levels matter: every threshold t in a run of empty levels
+// between non-empty levels i_k and i_{k+1} gives the same partition as
+// t = i_k, which is the smallest such t. So the levels are compacted to the
+// list of non-empty ones (i_0 < i_1 < ... < i_{M-1}), the objective is
+// evaluated once per entry k < M - 1 (threshold t = i_k), and the argmax over
+// entries is already the canonical threshold.
+template <class Sync>
 __device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, float q, float* __restrict__ curve,
-                                       SearchSmem& sm) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+                                       SearchSmem& sm, float2* __restrict__ sT, int2* __restrict__ sIC,
+                                       const DfTables* __restrict__ T) {
+    const int tid = Sync::tid(), lane = tid & 31, warp = tid >> 5;
     const bool shannon = (q == 1.0f);
-    const int base = tid * kBinsPerThread;
 
-    // ---- 1. counts and FP32 terms of this thread's levels
-    int hv[kBinsPerThread];
-    float a0[kBinsPerThread];  // term h^q; later the error band
-    float a1[kBinsPerThread];  // class-1 sum Q_1(t); later phi(t)
-    long long c = 0;
-    F2 w{0.f, 0.f};
+    // ---- 1. compaction of the non-empty levels, and the total count N
+    {
+        const int base = tid * kBinsPerThread;
+        int hv[kBinsPerThread];
+        int nz = 0;
+        long long c = 0;
 #pragma unroll
-    for (int k = 0; k < kBinsPerThread; ++k) {
-        int i = base + k;
-        hv[k] = i < L ? __ldcg(h + i) : 0;
-        a0[k] = term_f32(hv[k], q, shannon);
-        c += hv[k];
-        w = f2_add_f(w, a0[k]);
+        for (int k = 0; k < kBinsPerThread; ++k) {
+            const int i = base + k;
+            hv[k] = i < L ? __ldcg(h + i) : 0;
+            nz += hv[k] > 0;
+            c += hv[k];
+        }
+        int nz_inc = nz;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, nz_inc, d);
+            if (lane >= d) nz_inc += o;
+        }
+        long long csum = c;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, d);
+        if (lane == 31) sm.red_i[warp] = nz_inc;
+        if (lane == 0) sm.cnt_pre[warp] = csum;
+        Sync::sync();
+        if (warp == 0) {
+            const int v = lane < kSearchWarps ? sm.red_i[lane] : 0;
+            int vi = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int o = __shfl_up_sync(0xffffffffu, vi, d);
+                if (lane >= d) vi += o;
+            }
+            long long cs = lane < kSearchWarps ? sm.cnt_pre[lane] : 0;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, d);
+            __syncwarp();
+            if (lane < kSearchWarps) sm.red_i[lane] = vi - v;   // exclusive warp offsets
+            if (lane == kSearchWarps - 1) sm.canon_t = vi;       // M
+            if (lane == 0) sm.total = cs;
+        }
+        Sync::sync();
+        int pos = sm.red_i[warp] + nz_inc - nz;
+#pragma unroll
+        for (int k = 0; k < kBinsPerThread; ++k)
+            if (hv[k] > 0) sIC[pos++] = make_int2(base + k, hv[k]);
+    }
+    Sync::sync();
+    const int M = sm.canon_t;
+    const long long N = sm.total;
+    if (curve != nullptr) {
+        // empty class 1 below the first non-empty level
+        const int first = M > 0 ? sIC[0].x : L;
+        for (int t = tid; t < first && t < L - 1; t += kSearchThreads) curve[t] = __int_as_float(0x7fc00000);
+    }
+    if (M < 2) {
+        if (curve != nullptr)
+            for (int t = tid; t < L - 1; t += kSearchThreads) curve[t] = __int_as_float(0x7fc00000);
+        Sync::sync();
+        return SearchResult{-1, 0.f, TSALLIS_ERR_NO_VALID_THRESHOLD};
     }
 
-    // ---- 2. block scans of thread totals
-    long long c_inc = warp_prefix_i64(c, lane);
-    F2 w_inc = warp_prefix_f2(w, lane);
-    F2 w_sinc = warp_suffix_f2(w, lane);
+    // ---- 2. each thread takes a contiguous run of at most 8 entries
+    const int per = (M + kSearchThreads - 1) / kSearchThreads;
+    const int j0 = min(tid * per, M), j1 = min(j0 + per, M);
+    const F2 LN = shannon ? F2{0.f, 0.f} : df_log2_count((unsigned)N, T);
+    long long c = 0;
+    F2 w{0.f, 0.f};
+    for (int j = j0; j < j1; ++j) {
+        const int cnt = sIC[j].y;
+        const F2 tk = shannon ? df_hlog2h((unsigned)cnt, T) : df_pow_ratio((unsigned)cnt, LN, q, T);
+        sT[j] = make_float2(tk.hi, tk.lo);
+        c += cnt;
+        w = f2_add(w, tk);
+    }
+    // block scans: counts (prefix), term sums (prefix and, separately, suffix)
+    const long long c_inc = warp_prefix_i64(c, lane);
+    const F2 w_inc = warp_prefix_f2(w, lane);
+    const F2 w_sinc = warp_suffix_f2(w, lane);
     if (lane == 31) { sm.cnt_pre[warp] = c_inc; sm.w_pre[warp] = w_inc; }
     if (lane == 0) sm.w_suf[warp] = w_sinc;
-    __syncthreads();
+    Sync::sync();
     if (warp == 0) {
-        long long cw = lane < kSearchWarps ? sm.cnt_pre[lane] : 0;
-        F2 ww = lane < kSearchWarps ? sm.w_pre[lane] : F2{0.f, 0.f};
-        F2 ws = lane < kSearchWarps ? sm.w_suf[lane] : F2{0.f, 0.f};
-        long long ci = warp_prefix_i64(cw, lane);
-        F2 wi = warp_prefix_f2(ww, lane);
-        F2 si = warp_suffix_f2(ws, lane);
+        const long long cw = lane < kSearchWarps ? sm.cnt_pre[lane] : 0;
+        const F2 ww = lane < kSearchWarps ? sm.w_pre[lane] : F2{0.f, 0.f};
+        const F2 ws = lane < kSearchWarps ? sm.w_suf[lane] : F2{0.f, 0.f};
+        const long long ci = warp_prefix_i64(cw, lane);
+        const F2 wi = warp_prefix_f2(ww, lane);
+        const F2 si = warp_suffix_f2(ws, lane);
         long long ce = __shfl_up_sync(0xffffffffu, ci, 1);
         F2 we = shfl_up_f2(wi, 1);
         F2 se = shfl_down_f2(si, 1);
         if (lane == 0) { ce = 0; we = F2{0.f, 0.f}; }
         if (lane == 31) se = F2{0.f, 0.f};
-        if (lane == kSearchWarps - 1) sm.total = ci;
         __syncwarp();
         if (lane < kSearchWarps) { sm.cnt_pre[lane] = ce; sm.w_pre[lane] = we; sm.w_suf[lane] = se; }
     }
-    __syncthreads();
-    const long long N = sm.total;
+    Sync::sync();
     long long c_before = __shfl_up_sync(0xffffffffu, c_inc, 1);
     F2 w_before = shfl_up_f2(w_inc, 1);
     F2 w_after = shfl_down_f2(w_sinc, 1);
@@ -127,177 +223,126 @@ __device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, flo
     w_before = f2_add(sm.w_pre[warp], w_before);
     w_after = f2_add(w_after, sm.w_suf[warp]);
 
-    // class-1 sums, forward
+    // ---- 3. FP32 objective per entry (threshold at its level) and error band
+    float qa_f[kBinsPerThread], phi[kBinsPerThread], err[kBinsPerThread];  // err < 0: invalid
     {
-        F2 s = w_before;
+        F2 sA = w_before;
 #pragma unroll
         for (int k = 0; k < kBinsPerThread; ++k) {
-            s = f2_add_f(s, a0[k]);
-            a1[k] = f2_val(s);
+            if (j0 + k < j1) {
+                const float2 tk = sT[j0 + k];
+                sA = f2_add(sA, F2{tk.x, tk.y});
+            }
+            qa_f[k] = f2_val(sA);
         }
     }
-    // ---- 3. objective and error bound per threshold; class-2 sums backward
     float best_v = 0.f;
     int best_i = -1;
     {
+        const float fN = (float)N;
         F2 sB = w_after;
-        long long na = c_before + c;  // class-1 count through the last level of the thread
-#pragma unroll
+        long long na = c_before + c;
+#pragma unroll 1
         for (int k = kBinsPerThread - 1; k >= 0; --k) {
-            const int t = base + k;
-            const long long nb = N - na;
-            const bool valid = (t <= L - 2) && na > 0 && nb > 0;
-            float f = 0.f, e = -1.f;  // e < 0 marks an invalid threshold
-            if (valid) {
-                const float qa = a1[k], qb = f2_val(sB);
-                const float fa = (float)na, fb = (float)nb;
-                if (shannon) {
-                    float lna = logf(fa), lnb = logf(fb);
-                    float sa = qa / fa, sb = qb / fb;
-                    f = (lna - sa) + (lnb - sb);
-                    e = shannon_err(lna, sa, lnb, sb, f);
-                } else {
-                    float ab = (qa / powf(fa, q)) * (qb / powf(fb, q));
-                    f = (1.0f - ab) / (q - 1.0f);
-                    e = tsallis_err(ab, f, q);
+            const int j = j0 + k;
+            float f = 0.f, e = -1.f;
+            if (j < j1) {
+                const long long nb = N - na;
+                if (j < M - 1) {   // class 2 is non-empty
+                    const float qa = qa_f[k], qb = f2_val(sB);
+                    const float fa = (float)na, fb = (float)nb;
+                    if (shannon) {
+                        const float ua = log2f(fa), ub = log2f(fb);
+                        const float va = qa / fa, vb = qb / fb;
+                        const float fb2 = (ua - va) + (ub - vb);
+                        f = 0.693147182f * fb2;
+                        e = shannon_err(ua, va, ub, vb, fb2);
+                    } else {
+                        // class powers scaled like the terms (2^64)
+                        const float ab = (qa / class_pow_f32(na, fN, LN, q, T)) * (qb / class_pow_f32(nb, fN, LN, q, T));
+                        f = (1.0f - ab) / (q - 1.0f);
+                        e = tsallis_err(ab, f, q);
+                    }
+                    argmax_merge(best_v, best_i, f, j);
                 }
-                argmax_merge(best_v, best_i, f, t);
+                const float2 tk = sT[j];
+                sB = f2_add(sB, F2{tk.x, tk.y});
+                na -= sIC[j].y;
             }
-            if (curve != nullptr && t <= L - 2) curve[t] = valid ? f : __int_as_float(0x7fc00000);
-            sB = f2_add_f(sB, a0[k]);
-            a0[k] = e;
-            a1[k] = f;
-            na -= hv[k];
+            phi[k] = f;
+            err[k] = e;
         }
     }
-    block_argmax_f(best_v, best_i, sm);
-    const int t32 = sm.red_i[0];
-    const float phi32 = sm.red_v[0];
-    __syncthreads();
-    if (t32 < 0) return SearchResult{-1, 0.f, TSALLIS_ERR_NO_VALID_THRESHOLD};
-
-    // owner of t32 publishes its class-1 count and error band
-    if (t32 >= base && t32 < base + kBinsPerThread) {
-        long long na = c_before;
-#pragma unroll
+    if (curve != nullptr) {
         for (int k = 0; k < kBinsPerThread; ++k) {
-            na += hv[k];
-            if (base + k == t32) { sm.best_na = na; sm.best_err = a0[k]; }
+            const int j = j0 + k;
+            if (j >= j1) break;
+            const int tb = sIC[j].x, te = (j + 1 < M) ? sIC[j + 1].x : L - 1;
+            const float v = err[k] >= 0.f ? phi[k] : __int_as_float(0x7fc00000);
+            for (int t = tb; t < te && t < L - 1; ++t) curve[t] = v;
         }
     }
-    __syncthreads();
-    const long long na_best = sm.best_na;
+    block_argmax_f<Sync>(best_v, best_i, sm);
+    const int j32 = sm.red_i[0];
+    const float phi32 = sm.red_v[0];
+    Sync::sync();
+    if (j32 >= j0 && j32 < j1) {
+#pragma unroll
+        for (int k = 0; k < kBinsPerThread; ++k)
+            if (j0 + k == j32) sm.best_err = err[k];
+    }
+    Sync::sync();
     const float lower = phi32 - sm.best_err;
 
-    // ---- 4. near-tie detection: another partition within the error bands
+    // ---- 4. candidates: other entries (other partitions) inside the error bands
     bool tie = false;
-    {
-        long long na = c_before;
 #pragma unroll
-        for (int k = 0; k < kBinsPerThread; ++k) {
-            na += hv[k];
-            if (a0[k] >= 0.f && na != na_best && a1[k] + a0[k] >= lower) tie = true;
-        }
-    }
-    const bool rerank = __syncthreads_or(tie) != 0;
+    for (int k = 0; k < kBinsPerThread; ++k)
+        if (err[k] >= 0.f && j0 + k != j32 && phi[k] + err[k] >= lower) tie = true;
+    const bool rerank = block_any<Sync>(tie, sm);
 
     int status = TSALLIS_OK;
     float phi_out = phi32;
-    long long na_win = na_best;
+    int jwin = j32;
     if (rerank) {
         status |= TSALLIS_STATUS_RERANKED;
-        const double qd = (double)q;
-        double dT[kBinsPerThread];
-        double dsum = 0.0;
-#pragma unroll
-        for (int k = 0; k < kBinsPerThread; ++k) {
-            dT[k] = term_f64(hv[k], qd, shannon);
-            dsum += dT[k];
-        }
-        double d_inc = warp_prefix_f64(dsum, lane);
-        double d_sinc = warp_suffix_f64(dsum, lane);
-        if (lane == 31) sm.d_pre[warp] = d_inc;
-        if (lane == 0) sm.d_suf[warp] = d_sinc;
-        __syncthreads();
-        if (warp == 0) {
-            double a = lane < kSearchWarps ? sm.d_pre[lane] : 0.0;
-            double b = lane < kSearchWarps ? sm.d_suf[lane] : 0.0;
-            double ai = warp_prefix_f64(a, lane);
-            double bi = warp_suffix_f64(b, lane);
-            double ae = __shfl_up_sync(0xffffffffu, ai, 1);
-            double be = __shfl_down_sync(0xffffffffu, bi, 1);
-            if (lane == 0) ae = 0.0;
-            if (lane == 31) be = 0.0;
-            __syncwarp();
-            if (lane < kSearchWarps) { sm.d_pre[lane] = ae; sm.d_suf[lane] = be; }
-        }
-        __syncthreads();
-        double d_before = __shfl_up_sync(0xffffffffu, d_inc, 1);
-        double d_after = __shfl_down_sync(0xffffffffu, d_sinc, 1);
-        if (lane == 0) d_before = 0.0;
-        if (lane == 31) d_after = 0.0;
-        d_before += sm.d_pre[warp];
-        d_after += sm.d_suf[warp];
-        // class-1 sums forward, then candidates backward with class-2 sums
-        double dA[kBinsPerThread];
-        {
-            double s = d_before;
-#pragma unroll
-            for (int k = 0; k < kBinsPerThread; ++k) {
-                s += dT[k];
-                dA[k] = s;
-            }
-        }
         double bv = 0.0;
         int bi = -1;
-        {
-            double sB = d_after;
-            long long na = c_before + c;
-#pragma unroll
-            for (int k = kBinsPerThread - 1; k >= 0; --k) {
-                const long long nb = N - na;
-                if (a0[k] >= 0.f && a1[k] + a0[k] >= lower) {
-                    const double QA = dA[k], QB = sB;
-                    double f;
-                    if (shannon) {
-                        f = (log((double)na) - QA / (double)na) + (log((double)nb) - QB / (double)nb);
-                    } else {
-                        double ab = (QA / pow((double)na, qd)) * (QB / pow((double)nb, qd));
-                        f = (1.0 - ab) / (qd - 1.0);
-                    }
-                    argmax_merge(bv, bi, f, base + k);
-                }
-                sB += dT[k];  // level k joins class 2 for threshold k-1
-                na -= hv[k];
-            }
-        }
-        block_argmax_d(bv, bi, sm);
-        const int tw = sm.red_i[0];
-        phi_out = (float)sm.red_dv[0];
-        __syncthreads();
-        if (tw >= base && tw < base + kBinsPerThread) {
-            long long na = c_before;
-#pragma unroll
-            for (int k = 0; k < kBinsPerThread; ++k) {
-                na += hv[k];
-                if (base + k == tw) sm.best_na = na;
-            }
-        }
-        __syncthreads();
-        na_win = sm.best_na;
-    }
-
-    // ---- 5. canonical threshold: smallest t with the winning class-1 count
-    int tmin = 0x7fffffff;
-    {
+        F2 sA = w_before;
         long long na = c_before;
-#pragma unroll
         for (int k = 0; k < kBinsPerThread; ++k) {
-            na += hv[k];
-            if (a0[k] >= 0.f && na == na_win && base + k < tmin) tmin = base + k;
+            const int j = j0 + k;
+            if (j >= j1) break;
+            const float2 tk = sT[j];
+            sA = f2_add(sA, F2{tk.x, tk.y});
+            na += sIC[j].y;
+            if (!(err[k] >= 0.f && phi[k] + err[k] >= lower)) continue;
+            F2 sB = w_after;
+            for (int i = j1 - 1; i > j; --i) {
+                const float2 ti = sT[i];
+                sB = f2_add(sB, F2{ti.x, ti.y});
+            }
+            const long long nb = N - na;
+            double f;
+            if (shannon) {
+                const double la = df_to_double(df_log2_count((unsigned)na, T));
+                const double lb = df_to_double(df_log2_count((unsigned)nb, T));
+                f = 0.6931471805599453 * ((la - df_to_double(sA) / (double)na) + (lb - df_to_double(sB) / (double)nb));
+            } else {
+                const double pa = df_to_double(df_pow_ratio((unsigned)na, LN, q, T));
+                const double pb = df_to_double(df_pow_ratio((unsigned)nb, LN, q, T));
+                const double ab = (df_to_double(sA) / pa) * (df_to_double(sB) / pb);
+                f = (1.0 - ab) / ((double)q - 1.0);
+            }
+            argmax_merge(bv, bi, f, j);
         }
+        block_argmax_d<Sync>(bv, bi, sm);
+        jwin = sm.red_i[0];
+        phi_out = (float)sm.red_dv[0];
+        Sync::sync();
     }
-    const int t_final = block_min_i(tmin, sm);
+    const int t_final = sIC[jwin].x;
+    Sync::sync();   // sIC / sT may be reused by the caller after this
     return SearchResult{t_final, phi_out, status};
 }
 

@@ -1,301 +1,436 @@
-// 1-D thresholding path: histogram, search and binarise tiles driven by one
-// persistent kernel with a work-item queue.
+// 1-D thresholding path: histogram, search and binarise fused in one
+// persistent kernel (two 512-thread blocks per SM).
 //
-// Work items are taken in order from a global ticket counter. For uniform
-// groups (slices of one volume, or the whole volume as one group) item k is
-//   step s = k / (2 * ntiles), r = k % (2 * ntiles)
-//   r <  ntiles : histogram tile r of group s
-//   r >= ntiles : binarise tile of group s - lag (tiles in reverse order, so
-//                 the most recently read part of the group is re-read first)
-// A histogram tile builds a shared-memory histogram of its voxels and adds
-// it to the group's histogram in global memory. The last tile of a group to
-// arrive runs the search for that group and publishes the threshold. A
-// binarise tile waits (bounded) for its group's threshold, then re-reads its
-// voxels, which are still in L2 when the group is a slice, and writes the mask
-// (Algorithm 1).
+// Work is split into tiles of a group's voxels (a group is one slice, or
+// the whole volume, or one volume of a batch). Each block repeatedly takes
+// one tile:
+//   * a binarise tile of the oldest group whose threshold is published, if
+//     it still has untaken tiles (per-group counters, a head pointer that
+//     only moves forward), so a slice is re-read while it is still in L2;
+//   * otherwise the next histogram tile (one global counter);
+//   * otherwise (every histogram tile is taken) it waits, bounded, for the
+//     oldest unfinished group's threshold.
+// A histogram tile counts its voxels into a shared-memory histogram and adds
+// it to the group's histogram in global memory. The block that adds the last
+// tile of a group runs the exhaustive search of section II-C on it (all 512
+// threads) and publishes the threshold. A binarise tile applies Algorithm 1.
 //
-// No waits can deadlock: every histogram item is taken before any binarise
-// item of the same group, and histogram items never wait.
+// Histogram tiles never wait, and a block waits for a threshold only after
+// every histogram tile has been taken by running blocks, so waits end.
+// Every wait is bounded in time; a wait that runs out is reported per group.
+#include <cmath>
+
 #include "common.cuh"
+#include "dfmath.cuh"
 #include "search1d.cuh"
 #include "kernels.h"
 
 namespace tsl {
 
 constexpr int kSegThreads = kSearchThreads;  // 512
+constexpr int kSegMinBlocks = 2;
 
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 
-__device__ __forceinline__ void accumulate8(uint4 r, int lo, int L, int* __restrict__ sh, int copy, int C,
-                                            unsigned& low) {
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// 16-byte read-only load that skips L1, with an L2 eviction policy.
+__device__ __forceinline__ uint4 ld_v4_policy(const void* p, unsigned long long pol) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+
+// ------------------------------------------------------------ tiles
+
+// Histogram of 8 voxels: clamp both 16-bit halves of each word to
+// [lo, hi] with packed min/max, then one shared-memory atomic per voxel at
+// shb[v] (shb = sh - lo, so shb[v] is level v - lo).
+__device__ __forceinline__ void hist8(uint4 r, unsigned LO2, unsigned HI2, int* shb) {
     const unsigned w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int v0 = (int)(short)(w[j] & 0xffffu);
-        const int v1 = ((int)w[j]) >> 16;
-        const int b0 = level_of(v0, lo, L), b1 = level_of(v1, lo, L);
-        if (b0 == 0) ++low; else atomicAdd(&sh[b0 * C + copy], 1);
-        if (b1 == 0) ++low; else atomicAdd(&sh[b1 * C + copy], 1);
+        const unsigned c = __vmins2(__vmaxs2(w[j], LO2), HI2);
+        atomicAdd(shb + (int)(short)(c & 0xffffu), 1);
+        atomicAdd(shb + (((int)c) >> 16), 1);
     }
 }
 
-// Histogram of n voxels at src into the shared histogram sh[L][C], then add
-// it to gdst[L] and leave sh zeroed.
-template <int C>
-__device__ void hist_tile(const int16_t* __restrict__ src, long long n, int lo, int L, int* __restrict__ sh,
-                          int* __restrict__ gdst) {
+__device__ __forceinline__ int clamp_level(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// n voxels at src into the block histogram.
+__device__ void hist_tile(const int16_t* __restrict__ src, long long n, int lo, int hi, int* shb,
+                          unsigned long long pol) {
     const int tid = threadIdx.x;
-    const int copy = (tid & 31) % C;
-    unsigned low = 0;
-    // scalar head up to 16-byte alignment
-    const int head = (int)lmin(n, (long long)((((16 - ((uintptr_t)src & 15)) & 15)) >> 1));
-    if (tid < head) {
-        int b = level_of(src[tid], lo, L);
-        if (b == 0) ++low; else atomicAdd(&sh[b * C + copy], 1);
-    }
-    const uint4* vsrc = reinterpret_cast<const uint4*>(src + head);
+    const unsigned LO2 = ((unsigned)lo & 0xffffu) * 0x10001u;
+    const unsigned HI2 = ((unsigned)hi & 0xffffu) * 0x10001u;
+    const int head = (int)lmin(n, ((16 - ((uintptr_t)src & 15)) & 15) >> 1);
+    if (tid < head) atomicAdd(shb + clamp_level(src[tid], lo, hi), 1);
+    const uint4* v = reinterpret_cast<const uint4*>(src + head);
     const long long nv = (n - head) >> 3;
     long long i = tid;
     for (; i + 3 * kSegThreads < nv; i += 4 * kSegThreads) {
-        uint4 r0 = ld_stream_keep(vsrc + i);
-        uint4 r1 = ld_stream_keep(vsrc + i + kSegThreads);
-        uint4 r2 = ld_stream_keep(vsrc + i + 2 * kSegThreads);
-        uint4 r3 = ld_stream_keep(vsrc + i + 3 * kSegThreads);
-        accumulate8(r0, lo, L, sh, copy, C, low);
-        accumulate8(r1, lo, L, sh, copy, C, low);
-        accumulate8(r2, lo, L, sh, copy, C, low);
-        accumulate8(r3, lo, L, sh, copy, C, low);
+        const uint4 r0 = ld_v4_policy(v + i, pol);
+        const uint4 r1 = ld_v4_policy(v + i + kSegThreads, pol);
+        const uint4 r2 = ld_v4_policy(v + i + 2 * kSegThreads, pol);
+        const uint4 r3 = ld_v4_policy(v + i + 3 * kSegThreads, pol);
+        hist8(r0, LO2, HI2, shb);
+        hist8(r1, LO2, HI2, shb);
+        hist8(r2, LO2, HI2, shb);
+        hist8(r3, LO2, HI2, shb);
     }
-    for (; i < nv; i += kSegThreads) accumulate8(ld_stream_keep(vsrc + i), lo, L, sh, copy, C, low);
-    // scalar tail
-    const long long tail0 = head + (nv << 3);
-    if (tail0 + tid < n) {
-        int b = level_of(src[tail0 + tid], lo, L);
-        if (b == 0) ++low; else atomicAdd(&sh[b * C + copy], 1);
-    }
-    // level 0 is counted in registers (the clamped air level is the hottest)
-    low = __reduce_add_sync(0xffffffffu, low);
-    if ((tid & 31) == 0 && low) atomicAdd(&sh[0], (int)low);
-    __syncthreads();
-    for (int b = tid; b < L; b += kSegThreads) {
-        int s = 0;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            s += sh[b * C + c];
-            sh[b * C + c] = 0;
-        }
-        if (s) atomicAdd(&gdst[b], s);
-    }
-    __syncthreads();
+    for (; i < nv; i += kSegThreads) hist8(ld_v4_policy(v + i, pol), LO2, HI2, shb);
+    const long long t0 = head + (nv << 3);
+    if (t0 + tid < n) atomicAdd(shb + clamp_level(src[t0 + tid], lo, hi), 1);
 }
 
-// Algorithm 1 on n voxels: mask = level <= t (polarity 0) or level >= t + 1
-// (polarity 1), where level = clamp(v - lo, 0, L-1) >> shift. With
-// 0 <= t <= (L-1 >> shift) - 1 both reduce to a compare of v with
-// T = lo + ((t + 1) << shift) - 1. t < 0 gives zeros.
+// Algorithm 1 on 8 voxels with packed 16x2 compares: byte = 1 where
+// v <= T (le) or v > T (!le).
+__device__ __forceinline__ uint2 mask8(uint4 r, unsigned T2, bool le) {
+    unsigned m0, m1, m2, m3;
+    if (le) {
+        m0 = __vcmples2(r.x, T2); m1 = __vcmples2(r.y, T2); m2 = __vcmples2(r.z, T2); m3 = __vcmples2(r.w, T2);
+    } else {
+        m0 = __vcmpgts2(r.x, T2); m1 = __vcmpgts2(r.y, T2); m2 = __vcmpgts2(r.z, T2); m3 = __vcmpgts2(r.w, T2);
+    }
+    // bytes 0 and 2 of each compare word hold one voxel each
+    return make_uint2(__byte_perm(m0, m1, 0x6420) & 0x01010101u, __byte_perm(m2, m3, 0x6420) & 0x01010101u);
+}
+
+// Level <= t in Algorithm 1 terms: level = clamp(v - lo, 0, L-1) >> shift,
+// so for 0 <= t < top level it is v <= lo + ((t + 1) << shift) - 1; at or
+// above the top level every voxel qualifies. Clamped to the int16 range
+// (v <= 32767 always holds).
+__device__ __forceinline__ int bin_threshold(int t, int lo, int L, int shift) {
+    const int T = (t >= ((L - 1) >> shift)) ? 32767 : lo + ((t + 1) << shift) - 1;
+    return T > 32767 ? 32767 : T;
+}
+
+// Algorithm 1 over n voxels. t < 0 (no valid threshold) writes zeros.
 __device__ void bin_tile(const int16_t* __restrict__ src, uint8_t* __restrict__ dst, long long n, int t, int lo,
-                         int L, int shift, int polarity) {
+                         int L, int shift, int polarity, unsigned long long pol) {
     const int tid = threadIdx.x;
-    // thresholds at or above the top level put every voxel in class 1
-    const int T = (t >= ((L - 1) >> shift)) ? 0x7fffffff : lo + ((t + 1) << shift) - 1;
+    const int T = bin_threshold(t, lo, L, shift);
+    const unsigned T2 = ((unsigned)T & 0xffffu) * 0x10001u;
+    const bool le = polarity == 0;
     const bool none = t < 0;
-    const unsigned want = polarity ? 0u : 1u;   // value written when v <= T
-    auto fg = [&](int v) -> unsigned { return none ? 0u : ((v <= T) ? want : 1u - want); };
-    const int head = (int)lmin(n, (long long)((((16 - ((uintptr_t)src & 15)) & 15)) >> 1));
-    if (tid < head) dst[tid] = (uint8_t)fg(src[tid]);
-    const uint4* vsrc = reinterpret_cast<const uint4*>(src + head);
-    uint8_t* vdst = dst + head;
+    auto one = [&](int x) -> uint8_t { return none ? 0 : (uint8_t)(((x <= T) == le) ? 1 : 0); };
+    const int head = (int)lmin(n, ((16 - ((uintptr_t)src & 15)) & 15) >> 1);
+    if (tid < head) dst[tid] = one(src[tid]);
+    const uint4* v = reinterpret_cast<const uint4*>(src + head);
+    uint8_t* d = dst + head;
     const long long nv = (n - head) >> 3;
-    auto one = [&](uint4 r, long long i) {
-        const unsigned w[4] = {r.x, r.y, r.z, r.w};
-        unsigned out[2] = {0u, 0u};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int v0 = (int)(short)(w[j] & 0xffffu);
-            const int v1 = ((int)w[j]) >> 16;
-            out[j >> 1] |= (fg(v0) | (fg(v1) << 8)) << ((j & 1) * 16);
-        }
-        st_stream(vdst + i * 8, make_uint2(out[0], out[1]));
-    };
     long long i = tid;
     for (; i + 3 * kSegThreads < nv; i += 4 * kSegThreads) {
-        uint4 r0 = ld_last_use(vsrc + i);
-        uint4 r1 = ld_last_use(vsrc + i + kSegThreads);
-        uint4 r2 = ld_last_use(vsrc + i + 2 * kSegThreads);
-        uint4 r3 = ld_last_use(vsrc + i + 3 * kSegThreads);
-        one(r0, i);
-        one(r1, i + kSegThreads);
-        one(r2, i + 2 * kSegThreads);
-        one(r3, i + 3 * kSegThreads);
+        const uint4 r0 = ld_v4_policy(v + i, pol);
+        const uint4 r1 = ld_v4_policy(v + i + kSegThreads, pol);
+        const uint4 r2 = ld_v4_policy(v + i + 2 * kSegThreads, pol);
+        const uint4 r3 = ld_v4_policy(v + i + 3 * kSegThreads, pol);
+        st_stream(d + i * 8, none ? make_uint2(0u, 0u) : mask8(r0, T2, le));
+        st_stream(d + (i + kSegThreads) * 8, none ? make_uint2(0u, 0u) : mask8(r1, T2, le));
+        st_stream(d + (i + 2 * kSegThreads) * 8, none ? make_uint2(0u, 0u) : mask8(r2, T2, le));
+        st_stream(d + (i + 3 * kSegThreads) * 8, none ? make_uint2(0u, 0u) : mask8(r3, T2, le));
     }
-    for (; i < nv; i += kSegThreads) one(ld_last_use(vsrc + i), i);
-    const long long tail0 = head + (nv << 3);
-    if (tail0 + tid < n) dst[tail0 + tid] = (uint8_t)fg(src[tail0 + tid]);
+    for (; i < nv; i += kSegThreads) st_stream(d + i * 8, none ? make_uint2(0u, 0u) : mask8(ld_v4_policy(v + i, pol), T2, le));
+    const long long t0 = head + (nv << 3);
+    if (t0 + tid < n) dst[t0 + tid] = one(src[t0 + tid]);
 }
 
-struct Item {
+// ------------------------------------------------------------ scheduling
+
+struct Work {
     int kind;   // 0 none, 1 histogram, 2 binarise
     int group;
     int tile;
+    int t;      // binarise threshold (-2: its wait ran out, skip)
 };
 
-__device__ __forceinline__ Item decode(const SegArgs& a, unsigned k) {
-    Item it{0, 0, 0};
-    if (a.worklist != nullptr) {
-        WorkItem w = a.worklist[k];
-        it.group = w.group;
-        it.kind = (w.tile < 0) ? 2 : 1;
-        it.tile = w.tile & 0x7fffffff;
-        return it;
-    }
-    const unsigned nt = (unsigned)a.ntiles;
-    if (a.phases == kPhaseHist || a.phases == kPhaseBin) {
-        it.group = (int)(k / nt);
-        it.tile = (int)(k % nt);
-        it.kind = a.phases == kPhaseHist ? 1 : 2;
-        if (it.kind == 2) it.tile = a.ntiles - 1 - it.tile;
-        return it;
-    }
-    const unsigned s = k / (2 * nt), r = k % (2 * nt);
-    if (r < nt) {
-        if ((int)s < a.ngroups) { it.kind = 1; it.group = (int)s; it.tile = (int)r; }
-    } else {
-        const int g = (int)s - a.lag;
-        if (g >= 0 && g < a.ngroups) { it.kind = 2; it.group = g; it.tile = a.ntiles - 1 - (int)(r - nt); }
-    }
-    return it;
+__device__ __forceinline__ int group_tiles(const SegArgs& a, int g) {
+    return a.groups != nullptr ? a.groups[g].ntiles : a.ntiles;
 }
 
-template <int C>
-__global__ void __launch_bounds__(kSegThreads, 2) k_segment1d(const SegArgs a) {
+// Histogram work item k -> (group, tile). Batches: binary search over the
+// groups' first-tile offsets.
+__device__ __forceinline__ void locate(const SegArgs& a, unsigned k, int& g, int& tile) {
+    if (a.groups == nullptr) {
+        g = (int)(k / (unsigned)a.ntiles);
+        tile = (int)(k % (unsigned)a.ntiles);
+        return;
+    }
+    int lo = 0, hi = a.ngroups - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((unsigned)a.groups[mid].tile_off <= k) lo = mid; else hi = mid - 1;
+    }
+    g = lo;
+    tile = (int)(k - (unsigned)a.groups[lo].tile_off);
+}
+
+// Binarise queue entries: bits 40..63 the launch tag (epoch + 1, 24 bits),
+// bits 20..39 the group, bits 0..19 the tile. An entry is valid for this
+// launch once its tag matches.
+__device__ __forceinline__ unsigned long long bq_pack(int epoch, int g, int tile) {
+    return ((unsigned long long)((epoch + 1) & 0xffffff) << 40) | ((unsigned long long)g << 20) | (unsigned)tile;
+}
+__device__ __forceinline__ bool bq_valid(unsigned long long e, int epoch) {
+    return (int)(e >> 40) == ((epoch + 1) & 0xffffff);
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Per-block scheduler state (lane 0 of the scheduler warp).
+struct SchedState {
+    long long pend;   // claimed binarise queue position not yet published (-1: none)
+    bool b_turn;      // alternate histogram and binarise items when both exist
+};
+
+// The next work item of this block (run by the scheduler lane).
+//
+// Histogram tiles come from one counter. When the block that completes a
+// group has published its threshold, it appends the group's binarise tiles
+// to a flat queue (one atomicAdd reserves the positions). Schedulers claim
+// queue positions with a single atomicAdd each; a claim made before the
+// position is published is kept pending while the scheduler keeps handing
+// out histogram tiles, so claims never block histogram progress. When both
+// kinds are available, a block alternates between them, which keeps each
+// slice's re-read close behind its first read (so it hits L2). Once every
+// histogram tile is taken, the scheduler waits (bounded) for its pending
+// position.
+__device__ Work next_work(const SegArgs& a, int epoch, SchedState& st) {
+    Work w{0, 0, 0, 0};
+    ScratchHeader* h = a.hdr;
+    if (a.phases == kPhaseHist) {
+        const unsigned k = atomicAdd(&h->h_next, 1u);
+        if (k < a.ntotal) { w.kind = 1; locate(a, k, w.group, w.tile); }
+        return w;
+    }
+    if (a.phases == kPhaseBin) {
+        const unsigned k = atomicAdd(&h->b_next, 1u);
+        if (k < a.ntotal) {
+            int tile;
+            locate(a, k, w.group, tile);
+            w.kind = 2;
+            w.tile = group_tiles(a, w.group) - 1 - tile;
+            w.t = a.t_in[w.group];
+        }
+        return w;
+    }
+    for (;;) {
+        if (st.pend >= 0) {
+            const unsigned long long e = ld_acquire_u64(&a.bq[st.pend]);
+            if (bq_valid(e, epoch)) {
+                w.kind = 2;
+                w.group = (int)((e >> 20) & 0xfffff);
+                w.tile = (int)(e & 0xfffff);
+                w.t = __ldcg(&a.t_out[w.group]);
+                st.pend = -1;
+                st.b_turn = false;
+                return w;
+            }
+        } else if (st.b_turn && *(volatile unsigned*)&h->b_next < *(volatile unsigned*)&h->b_tail) {
+            const unsigned k = atomicAdd(&h->b_next, 1u);
+            if (k < a.ntotal) { st.pend = k; continue; }
+        }
+        if (*(volatile unsigned*)&h->h_next < a.ntotal) {
+            const unsigned k = atomicAdd(&h->h_next, 1u);
+            if (k < a.ntotal) {
+                w.kind = 1;
+                locate(a, k, w.group, w.tile);
+                st.b_turn = true;
+                return w;
+            }
+        }
+        // every histogram tile is taken
+        if (st.pend < 0) {
+            const unsigned k = atomicAdd(&h->b_next, 1u);
+            if (k >= a.ntotal) return w;   // every binarise tile is claimed: done
+            st.pend = k;
+        }
+        // wait (bounded) for the pending position to be published
+        const unsigned long long t0 = globaltimer_ns();
+        unsigned ns = 64;
+        while (!bq_valid(ld_acquire_u64(&a.bq[st.pend]), epoch)) {
+            if (globaltimer_ns() - t0 > a.timeout_ns) {
+                // its group never completed in time: give the position up;
+                // the group reports TIMEOUT
+                atomicExch(&h->err, 1);
+                st.pend = -1;
+                break;
+            }
+            __nanosleep(ns);
+            if (ns < 2048) ns <<= 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------ the kernel
+
+constexpr int kBlockThreads = kSegThreads + 32;        // 544
+constexpr int kBarHandoff = 1;                         // scheduler + workers
+constexpr int kBarWork = 2;                            // workers only
+
+__device__ __forceinline__ void work_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(kBarWork), "n"(kSegThreads) : "memory");
+}
+__device__ __forceinline__ void handoff_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(kBarHandoff), "n"(kBlockThreads) : "memory");
+}
+using WorkSync = NamedSync<kBarWork, 0>;
+
+// Dynamic shared memory: the block histogram sh[kMaxBins], then the
+// search's scratch: double-float terms sT[kMaxBins] and the compacted
+// (level, count) list sIC[kMaxBins].
+__global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(const SegArgs a) {
     extern __shared__ int4 smem_raw[];
     int* sh = reinterpret_cast<int*>(smem_raw);
+    float2* sT = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem_raw) + kMaxBins * sizeof(int));
+    int2* sIC = reinterpret_cast<int2*>(sT + kMaxBins);
     __shared__ SearchSmem ssm;
-    __shared__ unsigned s_ticket;
-    __shared__ int s_flag, s_t;
+    __shared__ Work s_work[2];
+    __shared__ int s_last;
     const int tid = threadIdx.x;
     const int epoch = *(volatile int*)&a.hdr->epoch;
 
-    for (int i = tid; i < a.L * C; i += kSegThreads) sh[i] = 0;
+    for (int i = tid; i < kMaxBins; i += kBlockThreads) sh[i] = 0;
     __syncthreads();
 
-    for (;;) {
-        if (tid == 0) s_ticket = atomicAdd(&a.hdr->ticket, 1u);
-        __syncthreads();
-        const unsigned k = s_ticket;
-        if (k >= a.nticket) break;
-        const Item it = decode(a, k);
-        if (it.kind != 0) {
+    if (tid >= kSegThreads) {
+        // ================= scheduler warp: prepares item i + 1 while the
+        // workers process item i (double-buffered hand-off)
+        SchedState st{-1, false};
+        for (int i = 0;; ++i) {
+            if (tid == kSegThreads) s_work[i & 1] = next_work(a, epoch, st);
+            handoff_sync();
+            if (s_work[i & 1].kind == 0) break;
+        }
+    } else {
+        // ================= workers
+        const DfTables* dft = static_cast<const DfTables*>(a.df_tables);
+        const int hi = a.lo + a.L - 1 > 32767 ? 32767 : a.lo + a.L - 1;
+        int* shb = sh - a.lo;   // shb[v] is level v - lo
+        const unsigned long long pol_keep = policy_evict_last();
+        const unsigned long long pol_drop = policy_evict_first();
+        for (int i = 0;; ++i) {
+            handoff_sync();
+            const Work w = s_work[i & 1];
+            if (w.kind == 0) break;
             const int16_t* gvol;
             uint8_t* gmask;
             long long gn;
             if (a.groups != nullptr) {
-                const GroupDesc gd = a.groups[it.group];
+                const GroupDesc gd = a.groups[w.group];
                 gvol = gd.vol; gmask = gd.mask; gn = gd.nvox;
             } else {
-                gvol = a.vol + (long long)it.group * a.group_vox;
-                gmask = a.mask + (long long)it.group * a.group_vox;
+                gvol = a.vol + (long long)w.group * a.group_vox;
+                gmask = a.mask + (long long)w.group * a.group_vox;
                 gn = a.group_vox;
             }
-            const long long off = (long long)it.tile * a.tile_vox;
+            const long long off = (long long)w.tile * a.tile_vox;
             const long long n = lmin((long long)a.tile_vox, gn - off);
-            if (it.kind == 1) {
-                int* gh = a.ghist + (long long)it.group * a.L;
-                if (n > 0) hist_tile<C>(gvol + off, n, a.lo, a.L, sh, gh);
+            if (w.kind == 1) {
+                hist_tile(gvol + off, n, a.lo, hi, shb, pol_keep);
+                work_sync();
+                // add the block histogram to the group's, leave sh zeroed
+                int* gh = a.ghist + (long long)w.group * a.L;
+                for (int b = tid; b < a.L; b += kSegThreads) {
+                    const int c = sh[b];
+                    sh[b] = 0;
+                    if (c) atomicAdd(&gh[b], c);
+                }
                 if (a.phases & kPhaseSearch) {
                     __threadfence();
-                    __syncthreads();
+                    work_sync();
                     if (tid == 0) {
                         int last = 0;
-                        const bool skip = (a.flags & 1u) && it.group == 0 && it.tile == 0;
-                        if (skip) {
-                            atomicExch(&a.hdr->err, 1);
-                        } else {
-                            const int gt = a.groups != nullptr ? a.groups[it.group].ntiles : a.ntiles;
-                            last = atomicAdd(&a.arrive[it.group], 1) == gt - 1;
-                        }
-                        s_flag = last;
+                        if ((a.flags & 1u) && w.group == 0 && w.tile == 0) atomicExch(&a.hdr->err, 1);
+                        else last = atomicAdd(&a.arrive[w.group], 1) == group_tiles(a, w.group) - 1;
+                        s_last = last;
                     }
-                    __syncthreads();
-                    if (s_flag) {
+                    work_sync();
+                    if (s_last) {
+                        // this block completed the group: search it and publish
                         __threadfence();
-                        SearchResult r = search1d_block(gh, a.L, a.q,
-                                                        a.curve ? a.curve + (long long)it.group * (a.L - 1) : nullptr,
-                                                        ssm);
-                        // leave the group's scratch histogram zeroed for the next launch
-                        for (int b = tid; b < a.L; b += kSegThreads) gh[b] = 0;
+                        SearchResult r = search1d_block<WorkSync>(
+                            gh, a.L, a.q, a.curve ? a.curve + (long long)w.group * (a.L - 1) : nullptr, ssm, sT,
+                            sIC, dft);
+                        for (int b = tid; b < a.L; b += kSegThreads) gh[b] = 0;   // scratch left zeroed
+                        const int nt = group_tiles(a, w.group);
                         if (tid == 0) {
-                            a.t_out[it.group] = r.t;
-                            a.phi_out[it.group] = r.phi;
-                            a.status[it.group] = r.status;
-                            a.arrive[it.group] = 0;
+                            a.t_out[w.group] = r.t;
+                            a.phi_out[w.group] = r.phi;
+                            a.status[w.group] = r.status;
+                            a.arrive[w.group] = 0;
+                            a.done_flag[w.group] = epoch + 1;
+                            __threadfence();
+                            s_last = (int)atomicAdd(&a.hdr->b_tail, (unsigned)nt);
                         }
-                        __threadfence();
-                        __syncthreads();
-                        if (tid == 0) st_release(&a.ready[it.group], epoch + 1);
+                        work_sync();
+                        // the group's binarise tiles enter the queue, most
+                        // recently read tile first
+                        const int base = s_last;
+                        for (int j = tid; j < nt; j += kSegThreads)
+                            st_release_u64(&a.bq[base + j], bq_pack(epoch, w.group, nt - 1 - j));
                     }
                 }
-            } else {
-                if (tid == 0) {
-                    int t;
-                    if (a.phases & kPhaseSearch) {
-                        const unsigned long long t0 = globaltimer_ns();
-                        unsigned ns = 32;
-                        bool ok = true;
-                        while (ld_acquire(&a.ready[it.group]) != epoch + 1) {
-                            if (globaltimer_ns() - t0 > a.timeout_ns) { ok = false; break; }
-                            __nanosleep(ns);
-                            if (ns < 2048) ns <<= 1;
-                        }
-                        if (ok) {
-                            t = __ldcg(&a.t_out[it.group]);
-                        } else {
-                            // recorded now, reported by the last block once
-                            // nothing of this launch can still write the status
-                            a.tmo[it.group] = epoch + 1;
-                            atomicExch(&a.hdr->err, 1);
-                            t = -2;
-                        }
-                    } else {
-                        t = a.t_in[it.group];
-                    }
-                    s_t = t;
-                }
-                __syncthreads();
-                const int t = s_t;
-                if (t != -2 && n > 0) bin_tile(gvol + off, gmask + off, n, t, a.lo, a.L, a.bin_shift, a.polarity);
+            } else if (w.t != -2) {
+                bin_tile(gvol + off, gmask + off, n, w.t, a.lo, a.L, a.bin_shift, a.polarity, pol_drop);
+                if (tid == 0 && (a.phases & kPhaseSearch)) atomicAdd(&a.bdone[w.group], 1);
             }
+            work_sync();
         }
-        __syncthreads();
     }
 
-    // exit: the last block restores the scratch header for the next launch
+    // exit: the last block restores the scratch for the next launch
     __syncthreads();
     if (tid == 0) {
         __threadfence();
         const unsigned d = atomicAdd(&a.hdr->done, 1u);
-        s_flag = (d == gridDim.x - 1);
+        s_last = (d == gridDim.x - 1);
     }
     __syncthreads();
-    if (s_flag) {
+    if (s_last) {
         __threadfence();
-        if (*(volatile int*)&a.hdr->err && (a.phases & kPhaseSearch)) {
-            // a wait ran out: report it, then clear every group's arrival
-            // count and histogram
-            for (int g = tid; g < a.ngroups; g += kSegThreads) {
-                if (*(volatile int*)&a.tmo[g] == epoch + 1) {
+        const bool err = *(volatile int*)&a.hdr->err != 0;
+        if (a.phases & kPhaseSearch) {
+            for (int g = tid; g < a.ngroups; g += kBlockThreads) {
+                if (err && (*(volatile int*)&a.done_flag[g] != epoch + 1 ||
+                            *(volatile int*)&a.bdone[g] != group_tiles(a, g))) {
+                    // never searched (a skipped arrival) or not fully binarised in time
                     a.t_out[g] = -1;
                     a.phi_out[g] = 0.f;
                     a.status[g] = 5; /* TSALLIS_ERR_TIMEOUT */
                 }
-                a.arrive[g] = 0;
+                a.bdone[g] = 0;
+                if (err) a.arrive[g] = 0;
             }
-            const long long tot = (long long)a.ngroups * a.L;
-            for (long long i = tid; i < tot; i += kSegThreads) a.ghist[i] = 0;
+            if (err) {
+                // clear every group's histogram
+                const long long tot = (long long)a.ngroups * a.L;
+                for (long long i = tid; i < tot; i += kBlockThreads) a.ghist[i] = 0;
+            }
         }
         __syncthreads();
         if (tid == 0) {
-            a.hdr->ticket = 0;
+            a.hdr->h_next = 0;
+            a.hdr->b_next = 0;
+            a.hdr->b_tail = 0;
             a.hdr->done = 0;
             a.hdr->err = 0;
             a.hdr->epoch = epoch + 1;
@@ -307,10 +442,15 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_segment1d(const SegArgs a) {
 __global__ void __launch_bounds__(kSearchThreads) k_search1d(const int32_t* __restrict__ hist, long long nh, int L,
                                                              float q, int32_t* __restrict__ t_out,
                                                              float* __restrict__ phi_out,
-                                                             int32_t* __restrict__ status, float* __restrict__ curve) {
+                                                             int32_t* __restrict__ status, float* __restrict__ curve,
+                                                             const DfTables* __restrict__ dft) {
     __shared__ SearchSmem sm;
+    extern __shared__ int4 smem_search[];
+    float2* sT = reinterpret_cast<float2*>(smem_search);
+    int2* sIC = reinterpret_cast<int2*>(sT + kMaxBins);
     for (long long g = blockIdx.x; g < nh; g += gridDim.x) {
-        SearchResult r = search1d_block(hist + g * L, L, q, curve ? curve + g * (L - 1) : nullptr, sm);
+        SearchResult r = search1d_block<BlockSync>(hist + g * L, L, q, curve ? curve + g * (L - 1) : nullptr, sm,
+                                                   sT, sIC, dft);
         if (threadIdx.x == 0) {
             t_out[g] = r.t;
             phi_out[g] = r.phi;
@@ -320,44 +460,98 @@ __global__ void __launch_bounds__(kSearchThreads) k_search1d(const int32_t* __re
     }
 }
 
-int segment1d_threads() { return kSegThreads; }
-int segment1d_smem_bytes(int L, int copies) { return L * copies * (int)sizeof(int); }
-
-cudaError_t segment1d_occupancy(int copies, int L, int* blocks_per_sm) {
-    const int smem = segment1d_smem_bytes(L, copies);
-    switch (copies) {
-        case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_segment1d<1>, kSegThreads, smem);
-        case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_segment1d<2>, kSegThreads, smem);
-        case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_segment1d<4>, kSegThreads, smem);
-        default: return cudaErrorInvalidValue;
+// Test hook: the double-float power and log2 used by the search, for
+// checking their accuracy against an independent double-precision result.
+__global__ void k_probe_dfmath(const unsigned* __restrict__ h, long long n, unsigned N, float q,
+                               double* __restrict__ pw, double* __restrict__ lg, const DfTables* __restrict__ T) {
+    const F2 LN = df_log2_u32(N, T);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned x = h[i];
+        pw[i] = (x >= 1u && x <= N) ? df_to_double(df_pow_ratio(x, LN, q, T)) * 0x1p-64 : 0.0;
+        lg[i] = x >= 1u ? df_to_double(df_log2_u32(x, T)) : 0.0;
     }
 }
 
-template <int C>
-static cudaError_t launch_c(const SegArgs& a, int grid, cudaStream_t s) {
-    const int smem = segment1d_smem_bytes(a.L, C);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_segment1d<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
+// log2(h) as float pairs for 0 <= h <= n - 1 (h = 0 gives 0).
+__global__ void k_build_log2_table(float2* __restrict__ lt, int n, const DfTables* __restrict__ T) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const F2 v = i >= 1 ? df_log2_u32((unsigned)i, T) : F2{0.f, 0.f};
+        lt[i] = make_float2(v.hi, v.lo);
     }
-    k_segment1d<C><<<grid, kSegThreads, smem, s>>>(a);
+}
+
+cudaError_t build_log2_table(void* lt, int n, const void* tables, cudaStream_t s) {
+    k_build_log2_table<<<(n + 255) / 256, 256, 0, s>>>(static_cast<float2*>(lt), n,
+                                                       static_cast<const DfTables*>(tables));
     return cudaGetLastError();
 }
 
-cudaError_t launch_segment1d(const SegArgs& a, int grid, int copies, cudaStream_t s) {
-    switch (copies) {
-        case 1: return launch_c<1>(a, grid, s);
-        case 2: return launch_c<2>(a, grid, s);
-        case 4: return launch_c<4>(a, grid, s);
-        default: return cudaErrorInvalidValue;
+cudaError_t launch_probe_dfmath(const unsigned* h, long long n, unsigned N, float q, double* pw, double* lg,
+                                const void* tables, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_probe_dfmath<<<256, 256, 0, s>>>(h, n, N, q, pw, lg, static_cast<const DfTables*>(tables));
+    return cudaGetLastError();
+}
+
+int segment1d_threads() { return kBlockThreads; }
+int segment1d_smem_bytes(int L, int copies) {
+    (void)L;
+    (void)copies;
+    return kMaxBins * (int)(sizeof(int) + sizeof(float2) + sizeof(int2));
+}
+
+size_t df_tables_bytes() { return sizeof(DfTables); }
+
+// Host-side construction of the double-float tables (double precision libm,
+// split into float pairs).
+void df_tables_fill(void* host, const void* log2_table, int log2_table_max) {
+    DfTables* t = static_cast<DfTables*>(host);
+    t->lt = static_cast<const float2*>(log2_table);
+    t->lt_max = log2_table_max;
+    for (int j = 0; j < 128; ++j) {
+        const double c = 1.0 + (j + 0.5) / 128.0;
+        const float inv = (float)(1.0 / c);
+        const double lt = -std::log2((double)inv);
+        const float hi = (float)lt;
+        t->lg[j] = make_float4(inv, hi, (float)(lt - (double)hi), 0.f);
+    }
+    for (int j = 0; j < 65; ++j) {
+        const double v = std::exp2((j - 32) / 64.0);
+        const float hi = (float)v;
+        t->ex[j] = make_float2(hi, (float)(v - (double)hi));
     }
 }
 
+// Opts every kernel variant into the shared memory it uses (above the
+// default 48 KB). Per device: call with that device current.
+cudaError_t segment1d_prepare() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_segment1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  segment1d_smem_bytes(kMaxBins, 1))) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_search1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMaxBins * (int)(sizeof(float2) + sizeof(int2)));
+}
+
+cudaError_t segment1d_occupancy(int copies, int L, int* blocks_per_sm) {
+    (void)L;
+    if (copies != 1) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_segment1d, kBlockThreads,
+                                                         segment1d_smem_bytes(kMaxBins, 1));
+}
+
+cudaError_t launch_segment1d(const SegArgs& a, int grid, int copies, cudaStream_t s) {
+    if (copies != 1) return cudaErrorInvalidValue;
+    k_segment1d<<<grid, kBlockThreads, segment1d_smem_bytes(kMaxBins, 1), s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_search1d(const int32_t* hist, long long nh, int L, float q, int32_t* t, float* phi,
-                            int32_t* status, float* curve, cudaStream_t s) {
+                            int32_t* status, float* curve, const void* tables, cudaStream_t s) {
     if (nh <= 0) return cudaSuccess;
     const int grid = (int)(nh < 65535 ? nh : 65535);
-    k_search1d<<<grid, kSearchThreads, 0, s>>>(hist, nh, L, q, t, phi, status, curve);
+    const int smem = kMaxBins * (int)(sizeof(float2) + sizeof(int2));
+    k_search1d<<<grid, kSearchThreads, smem, s>>>(hist, nh, L, q, t, phi, status, curve,
+                                                  static_cast<const DfTables*>(tables));
     return cudaGetLastError();
 }
 
