@@ -46,7 +46,7 @@ def _peaks():
 
 def _kernel_source_sha():
     h = hashlib.sha256()
-    for name in ("common.cuh", "search1d.cuh", "seg1d.cu", "kernels.h"):
+    for name in ("common.cuh", "dfmath.cuh", "search1d.cuh", "seg1d.cu", "kernels.h"):
         with open(os.path.join(ROOT, "paper_2012_10684_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -183,7 +183,7 @@ def run_reference(args, rank, world):
     return 0
 
 
-def cpu_baseline(vol_np, seconds=10.0):
+def cpu_baseline(vol_np, seconds=12.0):
     import oracle
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     passes = 0
@@ -192,7 +192,7 @@ def cpu_baseline(vol_np, seconds=10.0):
         oracle.segment1d(vol_np, NX * NY, Q, nthreads=cores)
         passes += 1
         dt = time.perf_counter() - t0
-        if dt >= seconds or passes >= 200:
+        if dt >= seconds or passes >= 5000:
             break
     return {"value": passes * vol_np.size / dt, "unit": "voxels/s", "cores": cores, "kind": "oracle",
             "sample": "%d full passes over the 512x512x400 volume (per-slice, FP64 prefix mode, "
