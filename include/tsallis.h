@@ -187,6 +187,36 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* ctx, const tsallis_volume* h_v
                                      const tsallis_params* p, int32_t* d_t, float* d_phi, int32_t* d_status,
                                      cudaStream_t stream);
 
+/*
+ * tsallis_segment_static: tsallis_segment for callers that cannot allocate
+ * device memory. The paper has no counterpart; it exists for code whose
+ * device memory is all owned by someone else (a framework's memory pool, a
+ * pipeline that forbids allocation after start-up) or that must avoid the
+ * implicit synchronisation of cudaMalloc/cudaFree. tsallis_segment needs a
+ * context, and creating one allocates; this entry point takes no context and
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Its scratch is one fixed __device__ array inside the library (about 8.2 MB,
+ * held on every GPU that loads the library until the process exits). Limits
+ * that follow from it: at most 512 histograms per call (slices in per-slice
+ * mode) and at most 16384 work tiles of 65536 voxels (about 1.07e9 voxels in
+ * whole-volume mode); 1-D form only (two_d must be 0). Calls beyond those
+ * limits return TSALLIS_ERR_INVALID_ARG before anything is enqueued. Other
+ * arguments, outputs and statuses are as for tsallis_segment; the device is
+ * the current CUDA device.
+ *
+ * The first call on a device does a synchronous set-up (looks up the array's
+ * device address, clears it, writes constant tables, sets kernel
+ * attributes); make that first call before any stream capture. Later calls
+ * only enqueue one kernel. Every call uses the same array, which keeps the
+ * state the previous call left (the kernel leaves it ready for the next
+ * call), so calls that overlap in time on the GPU (on different streams, or
+ * from different threads) race and must not be issued.
+ */
+tsallis_status tsallis_segment_static(const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                                      const tsallis_params* p, uint8_t* d_mask, int32_t* d_t, float* d_phi,
+                                      int32_t* d_status, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif
