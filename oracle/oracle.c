@@ -71,6 +71,7 @@ int oracle_hist2d(const int16_t* vol, int64_t nx, int64_t ny, int64_t nz, int32_
     if (!vol || !hist || nx < 1 || ny < 1 || nz < 1 || shift < 0 || shift > 15) return 1;
     int32_t L2 = L1 >> shift;
     if (L2 < 2 || L2 > 256) return 1;
+    if (L1 & ((1 << shift) - 1)) return 1; /* grey levels b >> shift must stay below L2 */
     memset(hist, 0, sizeof(int64_t) * (size_t)L2 * (size_t)L2);
     int dz = nz > 1 ? 1 : 0;
     int64_t count = nz > 1 ? 27 : 9;

@@ -30,6 +30,10 @@ struct tsallis_ctx {
     void* batch_buf = nullptr;
     size_t batch_bytes = 0;
     void* df_tables = nullptr;    // double-float log2/exp2 tables (device)
+    // 2-D form: histograms, search tables and thresholds (grown on demand)
+    void* s2_buf = nullptr;
+    size_t s2_bytes = 0;
+    int hist2d_blocks_per_sm = 0;
     void* log2_table = nullptr;   // log2 of counts up to 2^18 as float pairs (device)
 };
 
@@ -66,6 +70,7 @@ tsallis_status check_params(const tsallis_params* p) {
         if (p->shift < 0 || p->shift > 15) return TSALLIS_ERR_INVALID_ARG;
         int L2 = p->nbins >> p->shift;
         if (L2 < 2 || L2 > 256) return TSALLIS_ERR_INVALID_ARG;
+        if (p->nbins & ((1 << p->shift) - 1)) return TSALLIS_ERR_INVALID_ARG;   // grey levels must fill [0, L2)
     }
     if (p->topk < 0) return TSALLIS_ERR_INVALID_ARG;
     if (p->flags & ~TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL) return TSALLIS_ERR_INVALID_ARG;
@@ -145,6 +150,75 @@ ScratchView view(tsallis_ctx* c) {
     return v;
 }
 
+// 2-D buffer: grows (never shrinks) to hold `bytes`; synchronises the device
+// before replacing a smaller buffer that earlier work may still use.
+tsallis_status ensure_s2(tsallis_ctx* c, size_t bytes) {
+    if (c->s2_buf && bytes <= c->s2_bytes) return TSALLIS_OK;
+    size_t cap = c->s2_bytes > 0 ? c->s2_bytes : (size_t)1 << 22;
+    while (cap < bytes) cap *= 2;
+    if (c->s2_buf) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
+        cudaFree(c->s2_buf);
+        c->s2_buf = nullptr;
+        c->s2_bytes = 0;
+    }
+    if (cudaMalloc(&c->s2_buf, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return TSALLIS_ERR_OOM;
+    }
+    c->s2_bytes = cap;
+    return TSALLIS_OK;
+}
+
+constexpr long long kSearch2dChunk = 64;   // histograms per 2-D search launch sequence
+inline int levels2(const tsallis_params* p) { return p->nbins >> p->shift; }
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+cudaError_t hist2d_enqueue(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                           const tsallis_params* p, int32_t* d_hist, long long nh, cudaStream_t stream) {
+    const int L2 = levels2(p);
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, (size_t)nh * L2 * L2 * sizeof(int32_t), stream);
+    if (e != cudaSuccess) return e;
+    Hist2dLaunch h;
+    h.vol = d_vol;
+    h.nx = (int)nx;
+    h.ny = (int)ny;
+    h.nz = (int)nz;
+    h.lo = p->lo;
+    h.L = p->nbins;
+    h.shift = p->shift;
+    h.per_slice = p->mode == TSALLIS_PER_SLICE;
+    h.hist = d_hist;
+    h.sm_count = c->sm_count;
+    h.blocks_per_sm = c->hist2d_blocks_per_sm;
+    return launch_hist2d(h, stream);
+}
+
+// Searches nh 2-D histograms in chunks that share one scratch area.
+cudaError_t search2d_enqueue(tsallis_ctx* c, void* scratch, const int32_t* d_hist, long long nh,
+                             const tsallis_params* p, int32_t* d_t, int32_t* d_tbin, float* d_phi, int32_t* d_status,
+                             float* d_curve, cudaStream_t stream) {
+    const int L2 = levels2(p);
+    const long long cells = (long long)L2 * L2, m2 = (long long)(L2 - 1) * (L2 - 1);
+    for (long long k0 = 0; k0 < nh; k0 += kSearch2dChunk) {
+        Search2dLaunch s;
+        s.K = nh - k0 < kSearch2dChunk ? nh - k0 : kSearch2dChunk;
+        s.hist = d_hist + k0 * cells;
+        s.L2 = L2;
+        s.q = p->q;
+        s.tables = c->df_tables;
+        s.scratch = scratch;
+        s.curve = d_curve ? d_curve + k0 * m2 : nullptr;
+        s.t = d_t + 2 * k0;
+        s.t_bin = d_tbin ? d_tbin + k0 : nullptr;
+        s.phi = d_phi + k0;
+        s.status = d_status + k0;
+        const cudaError_t e = launch_search2d(s, stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 int grid_for(tsallis_ctx* c, unsigned nitems) {
     long long g = (long long)c->sm_count * (c->blocks_per_sm > 0 ? c->blocks_per_sm : 1);
     if ((long long)nitems < g) g = nitems;
@@ -158,6 +232,7 @@ void fill_common(SegArgs& a, const tsallis_params* p, tsallis_ctx* c) {
     a.q = p->q;
     a.polarity = p->polarity;
     a.bin_shift = 0;
+    a.t_stride = 1;
     a.flags = p->flags;
     a.timeout_ns = c->timeout_ns;
     a.tile_vox = c->tile_vox;
@@ -165,6 +240,44 @@ void fill_common(SegArgs& a, const tsallis_params* p, tsallis_ctx* c) {
 }
 
 tsallis_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TSALLIS_OK : TSALLIS_ERR_CUDA; }
+
+// 2-D steps 1-4: histogram kernel, search kernels, then the binarise phase
+// of the 1-D persistent kernel on the grey levels. The 2-D buffer holds the
+// histograms, the search tables and the thresholds t alone.
+tsallis_status segment2d(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                         const tsallis_params* p, long long ng, long long gvox, uint8_t* d_mask, int32_t* d_t,
+                         float* d_phi, int32_t* d_status, cudaStream_t stream) {
+    const int L2 = levels2(p);
+    const long long K = ng < kSearch2dChunk ? ng : kSearch2dChunk;
+    const size_t hist_bytes = align256((size_t)ng * L2 * L2 * sizeof(int32_t));
+    const size_t tbin_bytes = align256((size_t)ng * sizeof(int32_t));
+    const size_t search_bytes = search2d_scratch_bytes(L2, K);
+    tsallis_status st;
+    if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
+    if ((st = ensure_s2(c, hist_bytes + tbin_bytes + search_bytes)) != TSALLIS_OK) return st;
+    unsigned char* b = static_cast<unsigned char*>(c->s2_buf);
+    int32_t* hist = reinterpret_cast<int32_t*>(b);
+    int32_t* tbin = reinterpret_cast<int32_t*>(b + hist_bytes);
+    void* search = b + hist_bytes + tbin_bytes;
+    cudaError_t e = hist2d_enqueue(c, d_vol, nx, ny, nz, p, hist, ng, stream);
+    if (e == cudaSuccess) e = search2d_enqueue(c, search, hist, ng, p, d_t, tbin, d_phi, d_status, nullptr, stream);
+    if (e != cudaSuccess) return TSALLIS_ERR_CUDA;
+    SegArgs a;
+    fill_common(a, p, c);
+    a.bin_shift = p->shift;
+    a.vol = d_vol;
+    a.mask = d_mask;
+    a.group_vox = gvox;
+    a.ngroups = (int)ng;
+    a.ntiles = (int)((gvox + a.tile_vox - 1) / a.tile_vox);
+    a.phases = kPhaseBin;
+    if (ng * a.ntiles > 0xffffffffll) return TSALLIS_ERR_INVALID_ARG;
+    a.ntotal = (unsigned)(ng * a.ntiles);
+    a.t_in = tbin;
+    ScratchView v = view(c);
+    a.hdr = v.hdr;
+    return cuda_status(launch_segment1d(a, grid_for(c, a.ntotal), c->copies, stream));
+}
 
 }  // namespace
 
@@ -228,6 +341,12 @@ tsallis_status tsallis_create(tsallis_ctx** out, int device) {
         return TSALLIS_ERR_CUDA;
     }
     c->blocks_per_sm = c->max_blocks_per_sm;
+    if (seg2d_prepare() != cudaSuccess || hist2d_occupancy(&c->hist2d_blocks_per_sm) != cudaSuccess ||
+        c->hist2d_blocks_per_sm < 1) {
+        cudaGetLastError();
+        delete c;
+        return TSALLIS_ERR_CUDA;
+    }
     // double-float tables: the small reduction tables (host-built), then a
     // log2 table of counts up to 2^18 computed on the device from them
     std::vector<unsigned char> tab(df_tables_bytes());
@@ -257,6 +376,7 @@ void tsallis_destroy(tsallis_ctx* c) {
         DeviceGuard g(c->device);
         if (c->scratch) cudaFree(c->scratch);
         if (c->batch_buf) cudaFree(c->batch_buf);
+        if (c->s2_buf) cudaFree(c->s2_buf);
         if (c->df_tables) cudaFree(c->df_tables);
         if (c->log2_table) cudaFree(c->log2_table);
     }
@@ -286,7 +406,6 @@ tsallis_status tsallis_histogram(tsallis_ctx* c, const int16_t* d_vol, int64_t n
     if (nz == 0) return TSALLIS_OK;
     if (!d_vol || !d_hist) return TSALLIS_ERR_INVALID_ARG;
     if (!aligned16(d_vol)) return TSALLIS_ERR_ALIGNMENT;
-    if (p->two_d) return TSALLIS_ERR_UNIMPLEMENTED;
     const long long slice = nx * ny;
     const long long gvox = p->mode == TSALLIS_PER_SLICE ? slice : slice * nz;
     const long long ng = p->mode == TSALLIS_PER_SLICE ? nz : 1;
@@ -294,6 +413,7 @@ tsallis_status tsallis_histogram(tsallis_ctx* c, const int16_t* d_vol, int64_t n
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
+    if (p->two_d) return cuda_status(hist2d_enqueue(c, d_vol, nx, ny, nz, p, d_hist, ng, stream));
     if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
     if (cudaMemsetAsync(d_hist, 0, (size_t)ng * p->nbins * sizeof(int32_t), stream) != cudaSuccess)
         return TSALLIS_ERR_CUDA;
@@ -319,10 +439,15 @@ tsallis_status tsallis_search(tsallis_ctx* c, const int32_t* d_hist, int64_t nh,
     if (nh < 0 || nh > (1ll << 31) - 1) return TSALLIS_ERR_INVALID_ARG;
     if (nh == 0) return TSALLIS_OK;
     if (!d_hist || !d_t || !d_phi || !d_status) return TSALLIS_ERR_INVALID_ARG;
-    if (p->two_d) return TSALLIS_ERR_UNIMPLEMENTED;
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
+    if (p->two_d) {
+        const long long K = nh < kSearch2dChunk ? nh : kSearch2dChunk;
+        if ((st = ensure_s2(c, search2d_scratch_bytes(levels2(p), K))) != TSALLIS_OK) return st;
+        return cuda_status(search2d_enqueue(c, c->s2_buf, d_hist, nh, p, d_t, nullptr, d_phi, d_status, d_curve,
+                                            stream));
+    }
     return cuda_status(launch_search1d(d_hist, nh, p->nbins, p->q, d_t, d_phi, d_status, d_curve, c->df_tables,
                                        stream));
 }
@@ -335,7 +460,6 @@ tsallis_status tsallis_binarize(tsallis_ctx* c, const int16_t* d_vol, int64_t nx
     if (nz == 0) return TSALLIS_OK;
     if (!d_vol || !d_mask || !d_t) return TSALLIS_ERR_INVALID_ARG;
     if (!aligned16(d_vol) || !aligned16(d_mask)) return TSALLIS_ERR_ALIGNMENT;
-    if (p->two_d) return TSALLIS_ERR_UNIMPLEMENTED;
     const long long slice = nx * ny;
     const long long gvox = p->mode == TSALLIS_PER_SLICE ? slice : slice * nz;
     const long long ng = p->mode == TSALLIS_PER_SLICE ? nz : 1;
@@ -346,6 +470,10 @@ tsallis_status tsallis_binarize(tsallis_ctx* c, const int16_t* d_vol, int64_t nx
     if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
     SegArgs a;
     fill_common(a, p, c);
+    if (p->two_d) {   // threshold t of each (t, s) pair, on the grey level
+        a.bin_shift = p->shift;
+        a.t_stride = 2;
+    }
     a.vol = d_vol;
     a.mask = d_mask;
     a.group_vox = gvox;
@@ -369,7 +497,6 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
     if (nz == 0) return TSALLIS_OK;
     if (!d_vol || !d_mask || !d_t || !d_phi || !d_status) return TSALLIS_ERR_INVALID_ARG;
     if (!aligned16(d_vol) || !aligned16(d_mask)) return TSALLIS_ERR_ALIGNMENT;
-    if (p->two_d) return TSALLIS_ERR_UNIMPLEMENTED;
     const long long slice = nx * ny;
     const long long gvox = p->mode == TSALLIS_PER_SLICE ? slice : slice * nz;
     const long long ng = p->mode == TSALLIS_PER_SLICE ? nz : 1;
@@ -377,6 +504,7 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
+    if (p->two_d) return segment2d(c, d_vol, nx, ny, nz, p, ng, gvox, d_mask, d_t, d_phi, d_status, stream);
     if ((st = ensure_scratch(c, ng, ng * ((gvox + c->tile_vox - 1) / c->tile_vox))) != TSALLIS_OK) return st;
     SegArgs a;
     fill_common(a, p, c);

@@ -75,7 +75,7 @@ __device__ __forceinline__ F2 df_ln2() { return {0.693147182464599609375f, -1.90
 __device__ __forceinline__ F2 df_log2e() { return {1.44269502162933349609375f, 1.925963033500011e-08f}; }
 
 // log2(h) for an integer h >= 1.
-__device__ __noinline__ F2 df_log2_u32(unsigned h, const DfTables* __restrict__ T) {
+static __device__ __noinline__ F2 df_log2_u32(unsigned h, const DfTables* __restrict__ T) {
     if (h == 1u) return {0.f, 0.f};
     F2 hh = df_from_u32(h);
     const int e = ((__float_as_int(hh.hi) >> 23) & 0xff) - 127;
@@ -137,7 +137,7 @@ constexpr int kTermScaleLog2 = 64;
 
 // 2^64 (h / N)^q for integers 1 <= h <= N, given LN = log2(N). Kept out of
 // line: it is called from several places and its body is long.
-__device__ __noinline__ F2 df_pow_ratio(unsigned h, F2 LN, float q, const DfTables* __restrict__ T) {
+static __device__ __noinline__ F2 df_pow_ratio(unsigned h, F2 LN, float q, const DfTables* __restrict__ T) {
     F2 lh = df_log2_count(h, T);
     F2 d = df_add(lh, F2{-LN.hi, -LN.lo});                // log2(h / N) <= 0
     F2 y = df_add(df_mul_f(d, q), F2{(float)kTermScaleLog2, 0.f});

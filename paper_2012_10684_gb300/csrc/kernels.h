@@ -58,6 +58,7 @@ struct SegArgs {
     unsigned long long* bq; // [ntotal] binarise queue (launch tag | group | tile)
     int* ghist;             // [ngroups][L]: histogram target (scratch or caller's)
     const int* t_in;        // binarise-only: caller's thresholds
+    int t_stride;           // entries between consecutive groups' thresholds in t_in
     int* t_out;
     float* phi_out;
     int* status;
@@ -81,5 +82,33 @@ int segment1d_threads();
 int segment1d_smem_bytes(int L, int copies);
 cudaError_t segment1d_occupancy(int copies, int L, int* blocks_per_sm);
 cudaError_t segment1d_prepare();
+
+// 2-D form (seg2d.cu).
+struct Hist2dLaunch {
+    const int16_t* vol;
+    int nx, ny, nz;
+    int lo, L, shift;
+    int per_slice;          // 1: one histogram per slice, 3x3 window; 0: one histogram, 3x3x3 window (nz > 1)
+    int* hist;              // [nh][L2][L2], zeroed by the caller
+    int sm_count, blocks_per_sm;
+};
+struct Search2dLaunch {
+    const int* hist;        // [K][L2][L2]
+    long long K;
+    int L2;
+    float q;
+    const void* tables;
+    void* scratch;          // search2d_scratch_bytes(L2, K)
+    float* curve;           // optional [K][L2-1][L2-1]
+    int* t;                 // [K][2]
+    int* t_bin;             // optional [K]
+    float* phi;
+    int* status;
+};
+cudaError_t seg2d_prepare();
+cudaError_t hist2d_occupancy(int* blocks_per_sm);
+cudaError_t launch_hist2d(const Hist2dLaunch& p, cudaStream_t s);
+size_t search2d_scratch_bytes(int L2, long long K);
+cudaError_t launch_search2d(const Search2dLaunch& p, cudaStream_t s);
 
 }  // namespace tsl

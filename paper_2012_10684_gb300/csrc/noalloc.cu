@@ -144,6 +144,7 @@ extern "C" tsallis_status tsallis_segment_static(const int16_t* d_vol, int64_t n
     a.q = p->q;
     a.polarity = p->polarity;
     a.bin_shift = 0;
+    a.t_stride = 1;
     a.phases = kPhaseHist | kPhaseSearch | kPhaseBin;
     a.flags = p->flags;
     a.timeout_ns = 1000000000ull;

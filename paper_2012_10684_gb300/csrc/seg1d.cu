@@ -228,7 +228,7 @@ __device__ Work next_work(const SegArgs& a, int epoch, SchedState& st) {
             locate(a, k, w.group, tile);
             w.kind = 2;
             w.tile = group_tiles(a, w.group) - 1 - tile;
-            w.t = a.t_in[w.group];
+            w.t = a.t_in[(long long)w.group * a.t_stride];
         }
         return w;
     }

@@ -1,0 +1,653 @@
+// 2-D form of the thresholding path (section II-C, "Tsallis entropy").
+//
+// The grey level of a voxel is f = b >> shift, b = clamp(v - lo, 0, L-1),
+// giving L2 = L >> shift <= 256 grey levels; its mean level is
+// g = floor(sum of f over the 3x3 in-slice window / 9), or over the 3x3x3
+// window / 27 in whole-volume mode, indices clamped at the borders. h(f, g)
+// is the 2-D histogram. For a pair (t, s), quadrant 1 is {f <= t, g <= s}
+// and quadrant 2 is {f > t, g > s}; the other two quadrants are ignored.
+// With Q_k the sum of h^q over quadrant k and N_k its count,
+//     phi(t, s) = (1 - a b) / (q - 1),  a = Q_1 / N_1^q,  b = Q_2 / N_2^q
+// (the pseudo-additive objective; Shannon limit at q = 1 as in 1-D). The
+// maximiser's t is the threshold of Algorithm 1, applied to f.
+//
+// Kernels:
+//   k_hist2d    the histogram. Each thread owns four adjacent columns and
+//               sweeps down a run of rows, keeping the 3-row window of
+//               horizontal 3-sums (over 1 or 3 slices) in registers as
+//               packed 16-bit lanes; neighbours across threads come by warp
+//               shuffles. Counts with |g - f| <= kBand (nearly all: the mean
+//               tracks the grey level away from edges) go to a band-shaped
+//               shared-memory histogram, the rest straight to global memory.
+//   k_s2_rows   per row f: the terms w = 2^64 (h / 2^31)^q as double-float
+//               pairs (h log2 h at q = 1) and the row prefix and suffix sums
+//               of terms and counts;
+//   k_s2_cols   per column: prefix over rows of the row prefixes (sums over
+//               [0..t] x [0..s]) and suffix over rows of the row suffixes
+//               (sums over [t..] x [s..]); quadrant-2 sums are accumulated
+//               from their own corner, never as a total minus quadrant 1;
+//   k_s2_eval   phi(t, s) in FP32 with its error bound for every pair, and
+//               per row t the best entry and the largest phi + error;
+//   k_s2_final  the FP32 maximum and its error band; every pair whose band
+//               reaches it is re-evaluated in FP64 from the double-float
+//               sums; the FP64 maximiser wins, and among pairs with its
+//               partition (the same quadrant counts) and the same value the
+//               smallest (t, s) is returned.
+#include <cmath>
+
+#include "common.cuh"
+#include "dfmath.cuh"
+#include "kernels.h"
+#include "../../include/tsallis.h"
+
+namespace tsl {
+
+namespace {
+
+constexpr int kBand = 32;                  // half-width of the shared-memory band
+constexpr int kBandW = 2 * kBand + 1;
+constexpr int kH2Threads = 512;
+constexpr int kH2RowsPerGroup = 16;        // rows one thread group sweeps per tile
+constexpr int kS2Threads = 256;            // >= L2
+constexpr float kFixedLog2N = 31.0f;       // terms scaled as (h / 2^31)^q: no total needed
+
+// ------------------------------------------------------------ histogram
+
+struct Hist2dArgs {
+    const int16_t* vol;
+    int nx, ny, nz;
+    int lo, hi;            // hi = min(lo + L - 1, 32767)
+    int shift, L2;
+    int per_slice;         // 1: histogram z of slice z; 0: one histogram
+    int qw;                // column quads per thread group (multiple of 32, <= 128)
+    int nxb, nyc;          // x blocks and y chunks per slice
+    long long ntiles;
+    int* ghist;            // [nh][L2][L2], zeroed by the caller
+};
+
+// Grey levels of two packed int16 voxels, in 16-bit lanes.
+__device__ __forceinline__ unsigned grey2(unsigned w, unsigned LO2, unsigned HI2, int shift, unsigned M2) {
+    return (__vsub2(__vmins2(__vmaxs2(w, LO2), HI2), LO2) >> shift) & M2;
+}
+__device__ __forceinline__ unsigned grey1(int v, int lo, int hi, int shift) {
+    v = v < lo ? lo : (v > hi ? hi : v);
+    return (unsigned)(v - lo) >> shift;
+}
+
+// Grey levels of columns x0 .. x0+3 of one row as two packed words
+// [f0 | f1 << 16], [f2 | f3 << 16]. Columns past the end repeat column nx-1
+// (the clamped index), which is also what the right border of the window
+// needs.
+template <bool kVec>
+__device__ __forceinline__ void grey_quad(const int16_t* __restrict__ row, int x0, int nx, unsigned LO2, unsigned HI2,
+                                          int shift, unsigned M2, unsigned& A, unsigned& B) {
+    unsigned w0, w1;
+    if (kVec) {   // nx % 4 == 0 and 8-byte aligned rows
+        const int xs = x0 < nx ? x0 : nx - 4;
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(row + xs));
+        w0 = v.x;
+        w1 = v.y;
+    } else {
+        const unsigned short* r = reinterpret_cast<const unsigned short*>(row);
+        const int xa = min(x0, nx - 1), xb = min(x0 + 1, nx - 1), xc = min(x0 + 2, nx - 1), xd = min(x0 + 3, nx - 1);
+        w0 = (unsigned)__ldg(r + xa) | ((unsigned)__ldg(r + xb) << 16);
+        w1 = (unsigned)__ldg(r + xc) | ((unsigned)__ldg(r + xd) << 16);
+    }
+    A = grey2(w0, LO2, HI2, shift, M2);
+    B = grey2(w1, LO2, HI2, shift, M2);
+}
+
+// Horizontal window sums of one row (summed over kDz-neighbourhood slices)
+// for the thread's four columns, packed: Ha = [H0 | H1], Hb = [H2 | H3];
+// and the centre slice's grey levels Fa, Fb.
+template <int kDz, bool kVec>
+__device__ __forceinline__ void row_sums(const Hist2dArgs& a, int z, int y, int x0, int lane, unsigned LO2,
+                                         unsigned HI2, unsigned M2, unsigned& Ha, unsigned& Hb, unsigned& Fa,
+                                         unsigned& Fb) {
+    const long long plane = (long long)a.nx * a.ny;
+    const int16_t* base = a.vol + (long long)y * a.nx;
+    unsigned A, B;
+    grey_quad<kVec>(base + z * plane, x0, a.nx, LO2, HI2, a.shift, M2, Fa, Fb);
+    A = Fa;
+    B = Fb;
+    if (kDz) {
+        const int zm = z > 0 ? z - 1 : 0, zp = z < a.nz - 1 ? z + 1 : a.nz - 1;
+        unsigned A1, B1, A2, B2;
+        grey_quad<kVec>(base + zm * plane, x0, a.nx, LO2, HI2, a.shift, M2, A1, B1);
+        grey_quad<kVec>(base + zp * plane, x0, a.nx, LO2, HI2, a.shift, M2, A2, B2);
+        A += A1 + A2;   // lanes stay below 3 * 255
+        B += B1 + B2;
+    }
+    // neighbours: column x0 - 1 and x0 + 4 (clamped at the volume border)
+    const bool left_in = x0 > 0, right_in = x0 + 4 < a.nx;
+    unsigned gl = __shfl_up_sync(0xffffffffu, B, 1) >> 16;
+    unsigned gr = __shfl_down_sync(0xffffffffu, A, 1) & 0xffffu;
+    const bool need = (lane == 0 && left_in) || (lane == 31 && right_in);
+    if (need) {
+        const int xe = lane == 0 ? min(x0 - 1, a.nx - 1) : x0 + 4;   // idle lanes stay in bounds
+        unsigned e = grey1(__ldg(base + z * plane + xe), a.lo, a.hi, a.shift);
+        if (kDz) {
+            const int zm = z > 0 ? z - 1 : 0, zp = z < a.nz - 1 ? z + 1 : a.nz - 1;
+            e += grey1(__ldg(base + zm * plane + xe), a.lo, a.hi, a.shift) +
+                 grey1(__ldg(base + zp * plane + xe), a.lo, a.hi, a.shift);
+        }
+        if (lane == 0) gl = e;
+        else gr = e;
+    }
+    if (!left_in) gl = A & 0xffffu;    // column -1 is column 0
+    if (!right_in) gr = B >> 16;       // column past the end repeats the last one
+    const unsigned mid = (A >> 16) | (B << 16);   // [g1 | g2]
+    Ha = ((A << 16) | gl) + A + mid;
+    Hb = mid + B + ((B >> 16) | (gr << 16));
+}
+
+// Band-shaped shared histogram: entry (f, g) with d = g - f + kBand in
+// [0, kBandW) lives at band[f * kBandW + d].
+__device__ __forceinline__ void count_voxel(int f, int g, int* band, int* gh, int L2) {
+    const int d = g - f + kBand;
+    if ((unsigned)d < (unsigned)kBandW) atomicAdd(band + f * kBandW + d, 1);
+    else atomicAdd(gh + f * L2 + g, 1);
+}
+
+__device__ void flush_band(int* band, int* gh, int L2) {
+    const int nb = L2 * kBandW;
+    for (int i = threadIdx.x; i < nb; i += kH2Threads) {
+        const int c = band[i];
+        if (c) {
+            const int f = i / kBandW, g = f + (i - f * kBandW) - kBand;
+            atomicAdd(gh + f * L2 + g, c);
+            band[i] = 0;
+        }
+    }
+}
+
+template <int kDz, bool kVec>
+__global__ void __launch_bounds__(kH2Threads, 2) k_hist2d(const Hist2dArgs a) {
+    extern __shared__ int band[];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < a.L2 * kBandW; i += kH2Threads) band[i] = 0;
+    __syncthreads();
+    constexpr unsigned kDiv = kDz ? 27u : 9u;
+    const unsigned LO2 = ((unsigned)a.lo & 0xffffu) * 0x10001u;
+    const unsigned HI2 = ((unsigned)a.hi & 0xffffu) * 0x10001u;
+    const unsigned M2 = (0xffffu >> a.shift) * 0x10001u;
+    const int group = tid / a.qw, cq = tid - group * a.qw;
+    const int rows_per_tile = (kH2Threads / a.qw) * kH2RowsPerGroup;
+    const long long t0 = (long long)blockIdx.x * a.ntiles / gridDim.x;
+    const long long t1 = (long long)(blockIdx.x + 1) * a.ntiles / gridDim.x;
+    int cur = -1;
+    for (long long t = t0; t < t1; ++t) {
+        const int xb = (int)(t % a.nxb);
+        const long long r = t / a.nxb;
+        const int yc = (int)(r % a.nyc);
+        const int z = (int)(r / a.nyc);
+        const int hidx = a.per_slice ? z : 0;
+        if (hidx != cur) {
+            if (cur >= 0) {
+                __syncthreads();
+                flush_band(band, a.ghist + (long long)cur * a.L2 * a.L2, a.L2);
+                __syncthreads();
+            }
+            cur = hidx;
+        }
+        int* gh = a.ghist + (long long)hidx * a.L2 * a.L2;
+        const int x0 = 4 * (xb * a.qw + cq);
+        const int ys = yc * rows_per_tile + group * kH2RowsPerGroup;
+        const int ye = min(ys + kH2RowsPerGroup, a.ny);
+        if (ys >= a.ny) continue;   // uniform per warp: a warp lies in one group
+        unsigned Rma, Rmb, R0a, R0b, F0a, F0b, Fxa, Fxb;
+        row_sums<kDz, kVec>(a, z, ys > 0 ? ys - 1 : 0, x0, lane, LO2, HI2, M2, Rma, Rmb, Fxa, Fxb);
+        row_sums<kDz, kVec>(a, z, ys, x0, lane, LO2, HI2, M2, R0a, R0b, F0a, F0b);
+        for (int y = ys; y < ye; ++y) {
+            unsigned Rna, Rnb, Fna, Fnb;
+            row_sums<kDz, kVec>(a, z, y + 1 < a.ny ? y + 1 : a.ny - 1, x0, lane, LO2, HI2, M2, Rna, Rnb, Fna, Fnb);
+            const unsigned Ta = Rma + R0a + Rna, Tb = Rmb + R0b + Rnb;   // lanes below 9 * 765
+            if (x0 < a.nx) {
+                count_voxel((int)(F0a & 0xffffu), (int)((Ta & 0xffffu) / kDiv), band, gh, a.L2);
+                if (x0 + 1 < a.nx) count_voxel((int)(F0a >> 16), (int)((Ta >> 16) / kDiv), band, gh, a.L2);
+                if (x0 + 2 < a.nx) count_voxel((int)(F0b & 0xffffu), (int)((Tb & 0xffffu) / kDiv), band, gh, a.L2);
+                if (x0 + 3 < a.nx) count_voxel((int)(F0b >> 16), (int)((Tb >> 16) / kDiv), band, gh, a.L2);
+            }
+            Rma = R0a; Rmb = R0b; R0a = Rna; R0b = Rnb; F0a = Fna; F0b = Fnb;
+        }
+    }
+    __syncthreads();
+    if (cur >= 0) flush_band(band, a.ghist + (long long)cur * a.L2 * a.L2, a.L2);
+}
+
+// ------------------------------------------------------------ search
+
+struct S2Args {
+    const int* hist;      // [K][L2][L2]
+    int L2;
+    float q;
+    const DfTables* T;
+    int* PC;              // [K][L2][L2] counts, then quadrant-1 counts
+    float2* PW;           // terms, then quadrant-1 term sums
+    int* SC;              // [K][L2][L2] counts, then quadrant-2 counts
+    float2* SW;
+    float* rphi;          // [K][L2]: per row t, best FP32 phi
+    float* rerr;          //           its error bound
+    float* rupper;        //           largest phi + error
+    int* rs;              //           its s (-1: no valid pair in the row)
+    float* curve;         // optional [K][L2-1][L2-1]
+    int* t_out;           // [K][2] (t, s)
+    int* t_bin;           // optional [K]: t alone, for the binarise pass
+    float* phi_out;
+    int* status;
+};
+
+__device__ __forceinline__ long long s2_off(const S2Args& a, int k) { return (long long)k * a.L2 * a.L2; }
+
+// Inclusive block scans over the 256 threads (one value per thread).
+struct ScanSmem {
+    int c[kS2Threads / 32];
+    F2 w[kS2Threads / 32];
+};
+__device__ __forceinline__ int warp_prefix_i32(int v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+__device__ __forceinline__ int warp_suffix_i32(int v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_down_sync(0xffffffffu, v, d);
+        if (lane + d < 32) v += o;
+    }
+    return v;
+}
+
+__device__ void block_scan(int c, F2 w, bool suffix, ScanSmem& sm, int& c_out, F2& w_out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kW = kS2Threads / 32;
+    int ci = suffix ? warp_suffix_i32(c, lane) : warp_prefix_i32(c, lane);
+    F2 wi = suffix ? warp_suffix_f2(w, lane) : warp_prefix_f2(w, lane);
+    const int edge = suffix ? 0 : 31;
+    if (lane == edge) { sm.c[warp] = ci; sm.w[warp] = wi; }
+    __syncthreads();
+    // carry from the other warps, summed in a fixed order
+    int cc = 0;
+    F2 wc{0.f, 0.f};
+    if (suffix) {
+        for (int j = kW - 1; j > warp; --j) { cc += sm.c[j]; wc = f2_add(sm.w[j], wc); }
+    } else {
+        for (int j = 0; j < warp; ++j) { cc += sm.c[j]; wc = f2_add(wc, sm.w[j]); }
+    }
+    __syncthreads();
+    c_out = ci + cc;
+    w_out = suffix ? f2_add(wi, wc) : f2_add(wc, wi);
+}
+
+__global__ void __launch_bounds__(kS2Threads) k_s2_rows(const S2Args a) {
+    __shared__ ScanSmem sm;
+    const int k = blockIdx.y, i = blockIdx.x, s = threadIdx.x;
+    const long long o = s2_off(a, k) + (long long)i * a.L2;
+    const int h = s < a.L2 ? __ldg(a.hist + o + s) : 0;
+    F2 w{0.f, 0.f};
+    if (h > 0) w = a.q == 1.0f ? df_hlog2h((unsigned)h, a.T) : df_pow_ratio((unsigned)h, F2{kFixedLog2N, 0.f}, a.q, a.T);
+    int c;
+    F2 ws;
+    block_scan(h, w, false, sm, c, ws);
+    if (s < a.L2) { a.PC[o + s] = c; a.PW[o + s] = make_float2(ws.hi, ws.lo); }
+    block_scan(h, w, true, sm, c, ws);
+    if (s < a.L2) { a.SC[o + s] = c; a.SW[o + s] = make_float2(ws.hi, ws.lo); }
+}
+
+// Column scans: 32 columns x 8 row chunks per block.
+__global__ void __launch_bounds__(256) k_s2_cols(const S2Args a) {
+    __shared__ int tcA[8][32], tcB[8][32];
+    __shared__ F2 twA[8][32], twB[8][32];
+    const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
+    const int k = blockIdx.y, s = blockIdx.x * 32 + c;
+    const int rc = (a.L2 + 7) / 8, i0 = min(r * rc, a.L2), i1 = min(i0 + rc, a.L2);
+    const long long o = s2_off(a, k);
+    int ca = 0, cb = 0;
+    F2 wa{0.f, 0.f}, wb{0.f, 0.f};
+    if (s < a.L2) {
+        for (int i = i0; i < i1; ++i) {
+            const long long e = o + (long long)i * a.L2 + s;
+            ca += a.PC[e];
+            const float2 x = a.PW[e];
+            wa = f2_add(wa, F2{x.x, x.y});
+        }
+        for (int i = i1 - 1; i >= i0; --i) {
+            const long long e = o + (long long)i * a.L2 + s;
+            cb += a.SC[e];
+            const float2 x = a.SW[e];
+            wb = f2_add(F2{x.x, x.y}, wb);
+        }
+    }
+    tcA[r][c] = ca; twA[r][c] = wa;
+    tcB[r][c] = cb; twB[r][c] = wb;
+    __syncthreads();
+    ca = 0; cb = 0;
+    wa = F2{0.f, 0.f}; wb = F2{0.f, 0.f};
+    for (int j = 0; j < r; ++j) { ca += tcA[j][c]; wa = f2_add(wa, twA[j][c]); }
+    for (int j = 7; j > r; --j) { cb += tcB[j][c]; wb = f2_add(twB[j][c], wb); }
+    if (s >= a.L2) return;
+    for (int i = i0; i < i1; ++i) {
+        const long long e = o + (long long)i * a.L2 + s;
+        ca += a.PC[e];
+        const float2 x = a.PW[e];
+        wa = f2_add(wa, F2{x.x, x.y});
+        a.PC[e] = ca;
+        a.PW[e] = make_float2(wa.hi, wa.lo);
+    }
+    for (int i = i1 - 1; i >= i0; --i) {
+        const long long e = o + (long long)i * a.L2 + s;
+        cb += a.SC[e];
+        const float2 x = a.SW[e];
+        wb = f2_add(F2{x.x, x.y}, wb);
+        a.SC[e] = cb;
+        a.SW[e] = make_float2(wb.hi, wb.lo);
+    }
+}
+
+// Quadrant sums of pair (t, s): quadrant 1 at [t][s] of the prefix tables,
+// quadrant 2 at [t+1][s+1] of the suffix tables.
+struct Quad {
+    int na, nb;
+    F2 qa, qb;
+};
+__device__ __forceinline__ Quad quad_sums(const S2Args& a, int k, int t, int s) {
+    const long long o = s2_off(a, k);
+    const long long ea = o + (long long)t * a.L2 + s, eb = o + (long long)(t + 1) * a.L2 + (s + 1);
+    const float2 x = a.PW[ea], y = a.SW[eb];
+    return Quad{a.PC[ea], a.SC[eb], F2{x.x, x.y}, F2{y.x, y.y}};
+}
+
+// FP32 objective and its error bound (the 1-D bound: the class sums are
+// double-float sums rounded once). err < 0 marks an empty quadrant.
+__device__ __forceinline__ void eval32(const Quad& u, float q, const DfTables* T, float& f, float& err) {
+    f = 0.f;
+    err = -1.f;
+    if (u.na <= 0 || u.nb <= 0) return;
+    const float qa = f2_val(u.qa), qb = f2_val(u.qb);
+    const float fa = (float)u.na, fb = (float)u.nb;
+    if (q == 1.0f) {
+        const float ua = log2f(fa), ub = log2f(fb);
+        const float va = qa / fa, vb = qb / fb;
+        const float fbits = (ua - va) + (ub - vb);
+        f = 0.693147182f * fbits;
+        err = shannon_err(ua, va, ub, vb, fbits);
+    } else {
+        const F2 LN{kFixedLog2N, 0.f};
+        const float fN = 2147483648.0f;
+        const float ab = (qa / class_pow_f32(u.na, fN, LN, q, T)) * (qb / class_pow_f32(u.nb, fN, LN, q, T));
+        f = (1.0f - ab) / (q - 1.0f);
+        err = tsallis_err(ab, f, q);
+    }
+}
+
+__device__ __forceinline__ double eval64(const Quad& u, float q, const DfTables* T) {
+    if (q == 1.0f) {
+        const double la = df_to_double(df_log2_count((unsigned)u.na, T));
+        const double lb = df_to_double(df_log2_count((unsigned)u.nb, T));
+        return 0.6931471805599453 *
+               ((la - df_to_double(u.qa) / (double)u.na) + (lb - df_to_double(u.qb) / (double)u.nb));
+    }
+    const F2 LN{kFixedLog2N, 0.f};
+    const double pa = df_to_double(df_pow_ratio((unsigned)u.na, LN, q, T));
+    const double pb = df_to_double(df_pow_ratio((unsigned)u.nb, LN, q, T));
+    const double ab = (df_to_double(u.qa) / pa) * (df_to_double(u.qb) / pb);
+    return (1.0 - ab) / ((double)q - 1.0);
+}
+
+struct RedSmem {
+    float v[kS2Threads / 32];
+    float u[kS2Threads / 32];
+    int i[kS2Threads / 32];
+    double dv[kS2Threads / 32];
+    int n[kS2Threads / 32];
+};
+
+__global__ void __launch_bounds__(kS2Threads) k_s2_eval(const S2Args a) {
+    __shared__ RedSmem sm;
+    const int k = blockIdx.y, t = blockIdx.x, s = threadIdx.x;
+    const int lane = s & 31, warp = s >> 5;
+    const int m = a.L2 - 1;
+    float f = 0.f, err = -1.f;
+    if (s < m) eval32(quad_sums(a, k, t, s), a.q, a.T, f, err);
+    if (a.curve && s < m) a.curve[((long long)k * m + t) * m + s] = err >= 0.f ? f : __int_as_float(0x7fc00000);
+    float bv = f, up = err >= 0.f ? f + err : -INFINITY;
+    int bi = err >= 0.f ? s : -1;
+    warp_argmax(bv, bi);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) up = fmaxf(up, __shfl_xor_sync(0xffffffffu, up, d));
+    if (lane == 0) { sm.v[warp] = bv; sm.i[warp] = bi; sm.u[warp] = up; }
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int kW = kS2Threads / 32;
+        bv = lane < kW ? sm.v[lane] : 0.f;
+        bi = lane < kW ? sm.i[lane] : -1;
+        up = lane < kW ? sm.u[lane] : -INFINITY;
+        warp_argmax(bv, bi);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) up = fmaxf(up, __shfl_xor_sync(0xffffffffu, up, d));
+        if (lane == 0) {
+            sm.i[0] = bi;
+            sm.v[0] = bv;
+            sm.u[0] = up;
+        }
+    }
+    __syncthreads();
+    const int best = sm.i[0];
+    if (s == best) a.rerr[(long long)k * a.L2 + t] = err;
+    if (s == 0) {
+        a.rphi[(long long)k * a.L2 + t] = sm.v[0];
+        a.rs[(long long)k * a.L2 + t] = best;
+        a.rupper[(long long)k * a.L2 + t] = sm.u[0];
+    }
+}
+
+// Block reductions for the final kernel.
+__device__ void red_argmax_f(float& v, int& i, RedSmem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    warp_argmax(v, i);
+    if (lane == 0) { sm.v[warp] = v; sm.i[warp] = i; }
+    __syncthreads();
+    v = lane < kS2Threads / 32 ? sm.v[lane] : 0.f;
+    i = lane < kS2Threads / 32 ? sm.i[lane] : -1;
+    warp_argmax(v, i);
+    __syncthreads();
+}
+__device__ void red_argmax_d(double& v, int& i, RedSmem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    warp_argmax(v, i);
+    if (lane == 0) { sm.dv[warp] = v; sm.i[warp] = i; }
+    __syncthreads();
+    v = lane < kS2Threads / 32 ? sm.dv[lane] : 0.0;
+    i = lane < kS2Threads / 32 ? sm.i[lane] : -1;
+    warp_argmax(v, i);
+    __syncthreads();
+}
+__device__ int red_min_i(int v, RedSmem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = __reduce_min_sync(0xffffffffu, v);
+    if (lane == 0) sm.n[warp] = v;
+    __syncthreads();
+    v = lane < kS2Threads / 32 ? sm.n[lane] : 0x7fffffff;
+    v = __reduce_min_sync(0xffffffffu, v);
+    __syncthreads();
+    return v;
+}
+__device__ int red_sum_i(int v, RedSmem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) sm.n[warp] = v;
+    __syncthreads();
+    v = lane < kS2Threads / 32 ? sm.n[lane] : 0;
+    v = __reduce_add_sync(0xffffffffu, v);
+    __syncthreads();
+    return v;
+}
+
+// Two FP64 values of one partition computed from differently associated
+// double-float sums agree to far better than this; distinct partitions
+// closer than this are near-ties.
+constexpr double kSamePartitionTol = 1e-10;
+
+__global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
+    __shared__ RedSmem sm;
+    const int k = blockIdx.x, tid = threadIdx.x;
+    const int m = a.L2 - 1;
+    const long long ro = (long long)k * a.L2;
+    // 1. FP32 maximum over rows (rows are already reduced; smallest t wins ties)
+    float bv = 0.f;
+    int bt = -1;
+    for (int t = tid; t < m; t += kS2Threads)
+        if (a.rs[ro + t] >= 0) argmax_merge(bv, bt, a.rphi[ro + t], t);
+    red_argmax_f(bv, bt, sm);
+    if (bt < 0) {
+        if (tid == 0) {
+            a.t_out[2 * k] = -1;
+            a.t_out[2 * k + 1] = -1;
+            if (a.t_bin) a.t_bin[k] = -1;
+            a.phi_out[k] = 0.f;
+            a.status[k] = TSALLIS_ERR_NO_VALID_THRESHOLD;
+        }
+        return;
+    }
+    const float lower = bv - a.rerr[ro + bt];
+    // 2. FP64 values of every pair inside the band; the FP64 maximiser
+    double dv = 0.0;
+    int di = -1, nband = 0;
+    for (int t = 0; t < m; ++t) {
+        if (!(a.rupper[ro + t] >= lower)) continue;   // uniform over the block
+        for (int s = tid; s < m; s += kS2Threads) {
+            const Quad u = quad_sums(a, k, t, s);
+            float f, err;
+            eval32(u, a.q, a.T, f, err);
+            if (err >= 0.f && f + err >= lower) {
+                ++nband;
+                argmax_merge(dv, di, eval64(u, a.q, a.T), t * m + s);
+            }
+        }
+    }
+    red_argmax_d(dv, di, sm);
+    nband = red_sum_i(nband, sm);
+    if (di < 0) {   // the FP32 maximiser is always inside its own band; kept as a guard
+        di = bt * m + a.rs[ro + bt];
+        dv = eval64(quad_sums(a, k, bt, a.rs[ro + bt]), a.q, a.T);
+    }
+    const int wt = di / m, ws = di - wt * m;
+    const Quad uw = quad_sums(a, k, wt, ws);
+    const double tol = kSamePartitionTol * fmax(fabs(dv), 1.0);
+    // 3. canonical pair: the smallest (t, s) with the winner's partition and value
+    int ci = 0x7fffffff;
+    for (int t = 0; t < m && t <= wt; ++t) {
+        if (!(a.rupper[ro + t] >= lower)) continue;
+        for (int s = tid; s < m; s += kS2Threads) {
+            if (t * m + s >= di) break;
+            const Quad u = quad_sums(a, k, t, s);
+            if (u.na != uw.na || u.nb != uw.nb) continue;
+            float f, err;
+            eval32(u, a.q, a.T, f, err);
+            if (err >= 0.f && f + err >= lower && fabs(eval64(u, a.q, a.T) - dv) <= tol) ci = min(ci, t * m + s);
+        }
+    }
+    ci = min(red_min_i(ci, sm), di);
+    if (tid == 0) {
+        const int t = ci / m, s = ci - (ci / m) * m;
+        a.t_out[2 * k] = t;
+        a.t_out[2 * k + 1] = s;
+        if (a.t_bin) a.t_bin[k] = t;
+        a.phi_out[k] = (float)dv;
+        a.status[k] = TSALLIS_OK | (nband > 1 ? TSALLIS_STATUS_RERANKED : 0);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ host side
+
+int hist2d_smem_bytes(int L2) { return L2 * kBandW * (int)sizeof(int); }
+
+cudaError_t seg2d_prepare() {
+    const int smem = hist2d_smem_bytes(256);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_hist2d<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_hist2d<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_hist2d<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_hist2d<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_hist2d(const Hist2dLaunch& p, cudaStream_t s) {
+    Hist2dArgs a;
+    a.vol = p.vol;
+    a.nx = p.nx;
+    a.ny = p.ny;
+    a.nz = p.nz;
+    a.lo = p.lo;
+    a.hi = p.lo + p.L - 1 < 32767 ? p.lo + p.L - 1 : 32767;
+    a.shift = p.shift;
+    a.L2 = p.L >> p.shift;
+    a.per_slice = p.per_slice;
+    const int nq = (p.nx + 3) / 4;
+    a.qw = nq >= 128 ? 128 : ((nq + 31) / 32) * 32;
+    a.nxb = (nq + a.qw - 1) / a.qw;
+    const int rows_per_tile = (kH2Threads / a.qw) * kH2RowsPerGroup;
+    a.nyc = (p.ny + rows_per_tile - 1) / rows_per_tile;
+    a.ntiles = (long long)p.nz * a.nyc * a.nxb;
+    a.ghist = p.hist;
+    const bool window3d = !p.per_slice && p.nz > 1;
+    const bool vec = (p.nx % 4) == 0 && ((uintptr_t)p.vol & 7u) == 0;
+    long long grid = (long long)p.sm_count * p.blocks_per_sm;
+    if (grid > a.ntiles) grid = a.ntiles;
+    if (grid < 1) grid = 1;
+    const int smem = hist2d_smem_bytes(a.L2);
+    if (window3d) {
+        if (vec) k_hist2d<1, true><<<(int)grid, kH2Threads, smem, s>>>(a);
+        else k_hist2d<1, false><<<(int)grid, kH2Threads, smem, s>>>(a);
+    } else {
+        if (vec) k_hist2d<0, true><<<(int)grid, kH2Threads, smem, s>>>(a);
+        else k_hist2d<0, false><<<(int)grid, kH2Threads, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t hist2d_occupancy(int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_hist2d<1, true>, kH2Threads,
+                                                         hist2d_smem_bytes(256));
+}
+
+size_t search2d_scratch_bytes(int L2, long long K) {
+    const size_t cells = (size_t)K * L2 * L2;
+    return cells * (2 * sizeof(int) + 2 * sizeof(float2)) + (size_t)K * L2 * 4 * sizeof(float) + 256;
+}
+
+cudaError_t launch_search2d(const Search2dLaunch& p, cudaStream_t s) {
+    const int L2 = p.L2;
+    const size_t cells = (size_t)p.K * L2 * L2;
+    unsigned char* b = static_cast<unsigned char*>(p.scratch);
+    S2Args a;
+    a.hist = p.hist;
+    a.L2 = L2;
+    a.q = p.q;
+    a.T = static_cast<const DfTables*>(p.tables);
+    a.PW = reinterpret_cast<float2*>(b);
+    a.SW = a.PW + cells;
+    a.PC = reinterpret_cast<int*>(a.SW + cells);
+    a.SC = a.PC + cells;
+    float* rows = reinterpret_cast<float*>(a.SC + cells);
+    a.rphi = rows;
+    a.rerr = rows + (size_t)p.K * L2;
+    a.rupper = rows + 2 * (size_t)p.K * L2;
+    a.rs = reinterpret_cast<int*>(rows + 3 * (size_t)p.K * L2);
+    a.curve = p.curve;
+    a.t_out = p.t;
+    a.t_bin = p.t_bin;
+    a.phi_out = p.phi;
+    a.status = p.status;
+    k_s2_rows<<<dim3(L2, (unsigned)p.K), kS2Threads, 0, s>>>(a);
+    k_s2_cols<<<dim3((L2 + 31) / 32, (unsigned)p.K), 256, 0, s>>>(a);
+    k_s2_eval<<<dim3(L2 - 1, (unsigned)p.K), kS2Threads, 0, s>>>(a);
+    k_s2_final<<<(unsigned)p.K, kS2Threads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace tsl

@@ -59,6 +59,14 @@ def test_hist2d_matches_scipy_box_sum(shape):
     assert np.array_equal(h, ref)
 
 
+def test_hist2d_rejects_levels_that_do_not_fill_the_grey_range():
+    # grey = b >> shift must index L >> shift levels, so L is a multiple of 2^shift
+    v = np.zeros((1, 4, 4), np.int16)
+    with pytest.raises(RuntimeError):
+        oracle.hist2d(v, -1024, 4001, 4)
+    assert oracle.hist2d(v, -1024, 4000, 4).shape == (250, 250)
+
+
 # ------------------------------------------------------------ objective pins
 
 @pytest.mark.parametrize("case", json.load(open(os.path.join(GOLDEN, "hand_examples.json")))["cases"],
