@@ -56,6 +56,9 @@ typedef enum {
 
 /* Extra bits OR-ed into d_status entries (low byte holds a tsallis_status). */
 #define TSALLIS_STATUS_RERANKED 0x100  /* FP64 re-rank decided between near-tied candidates */
+#define TSALLIS_STATUS_FIRST_PASS_EXACT 0x200  /* the mask written in the histogram pass with a
+                                                  predicted threshold was already exact, so the
+                                                  group was not read a second time */
 
 typedef enum {
     TSALLIS_PER_SLICE = 0,    /* one histogram and threshold per z slice */
@@ -114,6 +117,42 @@ tsallis_status tsallis_set_wait_timeout(tsallis_ctx* ctx, uint64_t ns);
  * (0 = as many as fit). Returns TSALLIS_ERR_INVALID_ARG outside those ranges.
  */
 tsallis_status tsallis_set_launch_shape(tsallis_ctx* ctx, int32_t tile_vox, int32_t blocks_per_sm);
+
+/*
+ * Kernel used by tsallis_segment for per-slice 1-D work (the paper has one
+ * GPU design; these are two GB300 designs of the same steps, with equal
+ * results):
+ *   TSALLIS_SLICE_KERNEL_AUTO (default): the persistent tile kernel;
+ *   TSALLIS_SLICE_KERNEL_TILES: the persistent tile kernel;
+ *   TSALLIS_SLICE_KERNEL_CLUSTER: the cluster kernel where it applies
+ *     (slices of at most 262144 voxels whose voxel count is a multiple of
+ *     8), else the tile kernel. Returns TSALLIS_ERR_UNIMPLEMENTED if the
+ *     device cannot run 8-CTA clusters.
+ * The cluster kernel holds each slice in the shared memory of an 8-CTA
+ * thread-block cluster between its histogram and its binarisation, so the
+ * volume is read from memory once; it is slower than the tile kernel
+ * (each cluster waits for its slice's search before taking the next).
+ */
+#define TSALLIS_SLICE_KERNEL_AUTO 0
+#define TSALLIS_SLICE_KERNEL_TILES 1
+#define TSALLIS_SLICE_KERNEL_CLUSTER 2
+tsallis_status tsallis_set_slice_kernel(tsallis_ctx* ctx, int32_t kind);
+
+/*
+ * First-pass binarisation with a predicted threshold in the tile kernel
+ * (off by default; on = 1). With it on, a histogram tile of a group also writes the
+ * group's mask with a predicted threshold t^ (the threshold of the group
+ * whose search finished most recently in the same call; groups that start
+ * before any search has finished get no prediction). Once the group's
+ * search gives t, the mask is exact if no voxel of the group has a level
+ * between t^ and t, or (per-slice groups of at most 2^20 voxels) when every
+ * voxel that lies between them is among those the first pass listed (levels
+ * within 8 of t^), which are then rewritten; the group's status carries
+ * TSALLIS_STATUS_FIRST_PASS_EXACT and the group is not read again.
+ * Otherwise the group is binarised again with t. Results are identical
+ * either way; only the memory traffic differs.
+ */
+tsallis_status tsallis_set_speculation(tsallis_ctx* ctx, int32_t on);
 
 /*
  * Step 1: histogram (section I "Thresholding", Fig. 2; 2-D: section II-C,

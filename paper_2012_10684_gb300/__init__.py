@@ -37,7 +37,9 @@ TSALLIS_ERR_TIMEOUT = 5
 TSALLIS_ERR_OOM = 6
 TSALLIS_ERR_UNIMPLEMENTED = 7
 TSALLIS_STATUS_RERANKED = 0x100
+TSALLIS_STATUS_FIRST_PASS_EXACT = 0x200
 TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL = 0x1
+SLICE_KERNELS = {"auto": 0, "tiles": 1, "cluster": 2}
 
 PER_SLICE, WHOLE_VOLUME = 0, 1
 MASK_LOW, MASK_HIGH = 0, 1
@@ -75,6 +77,8 @@ _SIGS = {
     "tsallis_destroy": ([_P], None),
     "tsallis_set_wait_timeout": ([_P, ctypes.c_uint64], ctypes.c_int),
     "tsallis_set_launch_shape": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "tsallis_set_slice_kernel": ([_P, ctypes.c_int32], ctypes.c_int),
+    "tsallis_set_speculation": ([_P, ctypes.c_int32], ctypes.c_int),
     "tsallis_histogram": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(Params), _P, _P], ctypes.c_int),
     "tsallis_search": ([_P, _P, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
     "tsallis_binarize": ([_P, _P, _I64, _I64, _I64, _P, ctypes.POINTER(Params), _P, _P], ctypes.c_int),
@@ -142,6 +146,18 @@ def set_launch_shape(tile_vox: int = 32768, blocks_per_sm: int = 0, device=None)
     """Launch shape of the persistent kernels (see tsallis_set_launch_shape)."""
     _check("tsallis_set_launch_shape",
            lib().tsallis_set_launch_shape(context(device), int(tile_vox), int(blocks_per_sm)))
+
+
+def set_slice_kernel(kind: str = "auto", device=None) -> None:
+    """Kernel for per-slice 1-D segmentation: "auto", "tiles" or "cluster"
+    (see tsallis_set_slice_kernel)."""
+    _check("tsallis_set_slice_kernel", lib().tsallis_set_slice_kernel(context(device), SLICE_KERNELS[kind]))
+
+
+def set_speculation(on: bool = False, device=None) -> None:
+    """First-pass binarisation with a predicted threshold in the tile kernel
+    (see tsallis_set_speculation)."""
+    _check("tsallis_set_speculation", lib().tsallis_set_speculation(context(device), 1 if on else 0))
 
 
 def tsallis_probe_dfmath(h: torch.Tensor, N: int, q: float):

@@ -35,6 +35,10 @@ struct tsallis_ctx {
     size_t s2_bytes = 0;
     int hist2d_blocks_per_sm = 0;
     void* log2_table = nullptr;   // log2 of counts up to 2^18 as float pairs (device)
+    // per-slice 1-D kernel: TSALLIS_SLICE_KERNEL_*; clusters that fit at once
+    int slice_kernel = TSALLIS_SLICE_KERNEL_AUTO;
+    int speculate = 0;            // tile kernel: binarise in the first pass with a predicted threshold
+    int cluster_max = 0;
 };
 
 namespace {
@@ -88,17 +92,21 @@ tsallis_status check_shape(int64_t nx, int64_t ny, int64_t nz) {
 
 // Grows the context's scratch so it holds at least ngroups groups and
 // ntiles work tiles. The layout depends only on the capacities (arrive,
-// done_flag, bdone [capg]; ghist [capg][kMaxLevels]; bq [capt]), so state
+// done_flag, bdone [capg]; that [capg]; ghist [capg][kMaxLevels]; bq [capt];
+// exc_n [capg]; exc [capg][kExcCap]), so state
 // left by one launch lines up with the next. New memory is zeroed; the
 // kernels keep it consistent between launches.
-size_t scratch_layout(long long capg, long long capt, size_t* ghist_off, size_t* bq_off) {
-    size_t off = sizeof(ScratchHeader) + (size_t)capg * 3 * sizeof(int);
+size_t scratch_layout(long long capg, long long capt, size_t* ghist_off, size_t* bq_off, size_t* exc_off = nullptr) {
+    size_t off = sizeof(ScratchHeader) + (size_t)capg * (3 * sizeof(int) + sizeof(unsigned long long));
     off = (off + 255) & ~size_t(255);
     if (ghist_off) *ghist_off = off;
     off += (size_t)capg * kMaxLevels * sizeof(int);
     off = (off + 255) & ~size_t(255);
     if (bq_off) *bq_off = off;
-    return off + (size_t)capt * sizeof(unsigned long long);
+    off += (size_t)capt * sizeof(unsigned long long);
+    off = (off + 255) & ~size_t(255);
+    if (exc_off) *exc_off = off;   // exc_n [capg], then exc [capg][kExcCap]
+    return off + (size_t)capg * sizeof(int) + (size_t)capg * kExcCap * sizeof(unsigned);
 }
 
 tsallis_status ensure_scratch(tsallis_ctx* c, long long ngroups, long long ntiles) {
@@ -132,21 +140,27 @@ struct ScratchView {
     int* arrive;
     int* done_flag;
     int* bdone;
+    unsigned long long* that;
     int* ghist;
     unsigned long long* bq;
+    int* exc_n;
+    unsigned* exc;
 };
 
 ScratchView view(tsallis_ctx* c) {
     char* b = (char*)c->scratch;
-    size_t goff = 0, qoff = 0;
-    scratch_layout(c->cap_groups, c->cap_tiles, &goff, &qoff);
+    size_t goff = 0, qoff = 0, eoff = 0;
+    scratch_layout(c->cap_groups, c->cap_tiles, &goff, &qoff, &eoff);
     ScratchView v;
     v.hdr = (ScratchHeader*)b;
     v.arrive = (int*)(b + sizeof(ScratchHeader));
     v.done_flag = v.arrive + c->cap_groups;
     v.bdone = v.done_flag + c->cap_groups;
+    v.that = reinterpret_cast<unsigned long long*>(v.bdone + c->cap_groups);
     v.ghist = (int*)(b + goff);
     v.bq = (unsigned long long*)(b + qoff);
+    v.exc_n = (int*)(b + eoff);
+    v.exc = (unsigned*)(v.exc_n + c->cap_groups);
     return v;
 }
 
@@ -279,6 +293,14 @@ tsallis_status segment2d(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64
     return cuda_status(launch_segment1d(a, grid_for(c, a.ntotal), c->copies, stream));
 }
 
+// The cluster kernel, when chosen, takes per-slice 1-D work whose slices
+// are whole 16-byte words and fit in one cluster's shared memory.
+bool use_slice_cluster(const tsallis_ctx* c, const tsallis_params* p, long long slice) {
+    if (c->slice_kernel != TSALLIS_SLICE_KERNEL_CLUSTER || c->cluster_max < 1) return false;
+    return p->mode == TSALLIS_PER_SLICE && !p->two_d && slice % 8 == 0 &&
+           slice <= (long long)kClusterCtas * kClusterPartVox;
+}
+
 }  // namespace
 
 extern "C" {
@@ -341,6 +363,10 @@ tsallis_status tsallis_create(tsallis_ctx** out, int device) {
         return TSALLIS_ERR_CUDA;
     }
     c->blocks_per_sm = c->max_blocks_per_sm;
+    if (slice_cluster_prepare() != cudaSuccess || slice_cluster_occupancy(&c->cluster_max) != cudaSuccess) {
+        cudaGetLastError();
+        c->cluster_max = 0;   // the tile kernel serves every shape
+    }
     if (seg2d_prepare() != cudaSuccess || hist2d_occupancy(&c->hist2d_blocks_per_sm) != cudaSuccess ||
         c->hist2d_blocks_per_sm < 1) {
         cudaGetLastError();
@@ -395,6 +421,21 @@ tsallis_status tsallis_set_launch_shape(tsallis_ctx* c, int32_t tile_vox, int32_
     if (blocks_per_sm < 0 || blocks_per_sm > c->max_blocks_per_sm) return TSALLIS_ERR_INVALID_ARG;
     c->tile_vox = tile_vox;
     c->blocks_per_sm = blocks_per_sm > 0 ? blocks_per_sm : c->max_blocks_per_sm;
+    return TSALLIS_OK;
+}
+
+tsallis_status tsallis_set_slice_kernel(tsallis_ctx* c, int32_t kind) {
+    if (!c || (kind != TSALLIS_SLICE_KERNEL_AUTO && kind != TSALLIS_SLICE_KERNEL_TILES &&
+               kind != TSALLIS_SLICE_KERNEL_CLUSTER))
+        return TSALLIS_ERR_INVALID_ARG;
+    if (kind == TSALLIS_SLICE_KERNEL_CLUSTER && c->cluster_max < 1) return TSALLIS_ERR_UNIMPLEMENTED;
+    c->slice_kernel = kind;
+    return TSALLIS_OK;
+}
+
+tsallis_status tsallis_set_speculation(tsallis_ctx* c, int32_t on) {
+    if (!c || (on != 0 && on != 1)) return TSALLIS_ERR_INVALID_ARG;
+    c->speculate = on;
     return TSALLIS_OK;
 }
 
@@ -505,6 +546,29 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
     if (p->two_d) return segment2d(c, d_vol, nx, ny, nz, p, ng, gvox, d_mask, d_t, d_phi, d_status, stream);
+    if (use_slice_cluster(c, p, slice)) {
+        if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
+        ClusterArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.vol = d_vol;
+        a.mask = d_mask;
+        a.slice_vox = slice;
+        a.part_vox = ((slice + kClusterCtas - 1) / kClusterCtas + 7) / 8 * 8;
+        a.nz = (int)nz;
+        a.lo = p->lo;
+        a.L = p->nbins;
+        a.q = p->q;
+        a.polarity = p->polarity;
+        a.flags = p->flags;
+        a.timeout_ns = c->timeout_ns;
+        a.hdr = view(c).hdr;
+        a.t_out = d_t;
+        a.phi_out = d_phi;
+        a.status = d_status;
+        a.df_tables = c->df_tables;
+        const int ncl = (int)(nz < c->cluster_max ? nz : c->cluster_max);
+        return cuda_status(launch_slice_cluster(a, ncl, stream));
+    }
     if ((st = ensure_scratch(c, ng, ng * ((gvox + c->tile_vox - 1) / c->tile_vox))) != TSALLIS_OK) return st;
     SegArgs a;
     fill_common(a, p, c);
@@ -521,6 +585,12 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
     a.arrive = v.arrive;
     a.done_flag = v.done_flag;
     a.bdone = v.bdone;
+    a.that = v.that;
+    a.spec = c->speculate;
+    a.exc = v.exc;
+    a.exc_n = v.exc_n;
+    a.exc_cap = kExcCap;
+    a.exc_w = gvox <= (1ll << 20) ? kExcWindow : 0;   // positions are kept in 20 bits
     a.bq = v.bq;
     a.ghist = v.ghist;
     a.t_out = d_t;

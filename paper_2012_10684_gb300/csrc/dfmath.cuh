@@ -120,9 +120,15 @@ __device__ __forceinline__ F2 df_exp2(F2 y, const DfTables* __restrict__ T) {
     return {ldexpf(r.hi, ki), ldexpf(r.lo, ki)};
 }
 
-// log2(h), from the table for small counts.
+// log2(h) of a count. kTable: counts up to lt_max are read from the table
+// in global memory; otherwise log2 is computed in registers. Both give the
+// same bits (the table is filled by df_log2_u32). The table saves
+// instructions where a load is cheap (a search kernel that runs alone);
+// computing avoids a dependent global load where the memory system is busy
+// (the search inside the streaming kernel).
+template <bool kTable>
 __device__ __forceinline__ F2 df_log2_count(unsigned h, const DfTables* __restrict__ T) {
-    if (h <= (unsigned)T->lt_max) {
+    if (kTable && h <= (unsigned)T->lt_max) {
         const float2 v = __ldg(&T->lt[h]);
         return {v.x, v.y};
     }
@@ -137,17 +143,19 @@ constexpr int kTermScaleLog2 = 64;
 
 // 2^64 (h / N)^q for integers 1 <= h <= N, given LN = log2(N). Kept out of
 // line: it is called from several places and its body is long.
+template <bool kTable>
 static __device__ __noinline__ F2 df_pow_ratio(unsigned h, F2 LN, float q, const DfTables* __restrict__ T) {
-    F2 lh = df_log2_count(h, T);
+    F2 lh = df_log2_count<kTable>(h, T);
     F2 d = df_add(lh, F2{-LN.hi, -LN.lo});                // log2(h / N) <= 0
     F2 y = df_add(df_mul_f(d, q), F2{(float)kTermScaleLog2, 0.f});
     return df_exp2(y, T);
 }
 
 // h * log2(h) as a float pair (the Shannon-limit term, in bits).
+template <bool kTable>
 __device__ __forceinline__ F2 df_hlog2h(unsigned h, const DfTables* __restrict__ T) {
     if (h <= 1u) return {0.f, 0.f};
-    return df_mul(df_from_u32(h), df_log2_count(h, T));
+    return df_mul(df_from_u32(h), df_log2_count<kTable>(h, T));
 }
 
 // FP32 class power 2^64 (n / N)^q for the objective's first pass. Small
@@ -155,9 +163,10 @@ __device__ __forceinline__ F2 df_hlog2h(unsigned h, const DfTables* __restrict__
 // low part of the exponent (within 3.5 ulp: exp2f is documented to 2 ulp);
 // larger ones use powf (documented to 4 ulp, plus 1.5 q ulp from rounding
 // n / N). Both stay inside the error band used by the search.
+template <bool kTable>
 __device__ __forceinline__ float class_pow_f32(long long n, float fN, F2 LN, float q, const DfTables* __restrict__ T) {
     if (n <= (long long)T->lt_max) {
-        const F2 y = df_mul_f(df_add(df_log2_count((unsigned)n, T), F2{-LN.hi, -LN.lo}), q);
+        const F2 y = df_mul_f(df_add(df_log2_count<kTable>((unsigned)n, T), F2{-LN.hi, -LN.lo}), q);
         return exp2f(y.hi) * __fmaf_rn(y.lo, 0.693147182f, 1.0f) * kTermScale;
     }
     return powf((float)n / fN, q) * kTermScale;

@@ -20,7 +20,9 @@ struct ScratchHeader {
     unsigned int done;    // blocks that have finished
     int epoch;            // launches so far; flags are compared to epoch + 1
     int err;              // a device wait ran out or an arrival was skipped
-    int pad[9];
+    unsigned long long latest;   // (epoch + 1) << 32 | (t + 1): the threshold found
+                                 // most recently in this launch (a prediction)
+    int pad[8];
 };
 
 enum Phase : int { kPhaseHist = 1, kPhaseSearch = 2, kPhaseBin = 4 };
@@ -55,6 +57,16 @@ struct SegArgs {
     int* arrive;            // [ngroups] histogram tiles added so far
     int* done_flag;         // [ngroups] epoch + 1 once the threshold is published
     int* bdone;             // [ngroups] binarise tiles finished
+    unsigned long long* that;  // [ngroups] (epoch + 1) << 32 | (t^ + 1): the predicted
+                               // threshold the group's first pass binarised with
+    int spec;               // 1: histogram tiles also binarise with a predicted threshold
+    // exceptions of the first pass: voxels whose level lies within exc_w of the
+    // predicted threshold, (position in group << 12) | (level - (t^ - exc_w + 1)),
+    // at most exc_cap per group; exc_w = 0: none are kept
+    unsigned* exc;          // [ngroups][exc_cap]
+    int* exc_n;             // [ngroups] entries appended (> exc_cap: overflowed)
+    int exc_cap;
+    int exc_w;
     unsigned long long* bq; // [ntotal] binarise queue (launch tag | group | tile)
     int* ghist;             // [ngroups][L]: histogram target (scratch or caller's)
     const int* t_in;        // binarise-only: caller's thresholds
@@ -82,6 +94,34 @@ int segment1d_threads();
 int segment1d_smem_bytes(int L, int copies);
 cudaError_t segment1d_occupancy(int copies, int L, int* blocks_per_sm);
 cudaError_t segment1d_prepare();
+constexpr int kExcCap = 8192;      // first-pass exceptions kept per group
+constexpr int kExcWindow = 8;      // levels on each side of the predicted threshold
+
+// Per-slice 1-D form with the slice held in a cluster's shared memory
+// (seg_cluster.cu): a cluster of kClusterCtas CTAs owns one slice, each CTA
+// at most kClusterPartVox voxels of it.
+constexpr int kClusterCtas = 8;
+constexpr int kClusterPartVox = 32768;
+struct ClusterArgs {
+    const int16_t* vol;     // [nz][slice_vox], 16-byte aligned, slice_vox % 8 == 0
+    uint8_t* mask;
+    long long slice_vox;    // N, voxels per slice (<= kClusterCtas * kClusterPartVox)
+    long long part_vox;     // voxels per CTA part: ceil(N / kClusterCtas) rounded up to 8
+    int nz;
+    int lo, L;
+    float q;
+    int polarity;
+    unsigned int flags;
+    unsigned long long timeout_ns;
+    ScratchHeader* hdr;     // h_next: next slice; done: finished CTAs (both reset by the kernel)
+    int* t_out;
+    float* phi_out;
+    int* status;
+    const void* df_tables;
+};
+cudaError_t slice_cluster_prepare();
+cudaError_t slice_cluster_occupancy(int* max_clusters);
+cudaError_t launch_slice_cluster(const ClusterArgs& a, int nclusters, cudaStream_t s);
 
 // 2-D form (seg2d.cu).
 struct Hist2dLaunch {

@@ -13,7 +13,8 @@
 //
 // The array lives in every GPU that loads the library, for the life of the
 // process. Its layout (sizes fixed at build time):
-//   ScratchHeader | arrive, done_flag, bdone [kMaxGroups] | ghist
+//   ScratchHeader | arrive, done_flag, bdone [kMaxGroups] | predicted
+//   thresholds [kMaxGroups] | ghist
 //   [kMaxGroups][4096] | binarise queue [kMaxTiles] | double-float tables |
 //   two-entry log2 table.
 // The kernel leaves every counter and histogram zeroed when it finishes
@@ -38,7 +39,8 @@ constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffArrive = sizeof(ScratchHeader);
-constexpr size_t kOffGhist = align256(kOffArrive + 3 * kMaxGroups * sizeof(int));
+constexpr size_t kOffThat = kOffArrive + 3 * kMaxGroups * sizeof(int);
+constexpr size_t kOffGhist = align256(kOffThat + kMaxGroups * sizeof(unsigned long long));
 constexpr size_t kOffQueue = align256(kOffGhist + (size_t)kMaxGroups * kMaxLevels * sizeof(int));
 constexpr size_t kOffTables = align256(kOffQueue + (size_t)kMaxTiles * sizeof(unsigned long long));
 constexpr size_t kTablesBytes = 4096;              // room for the double-float tables
@@ -153,6 +155,9 @@ extern "C" tsallis_status tsallis_segment_static(const int16_t* d_vol, int64_t n
     a.arrive = arrive;
     a.done_flag = arrive + kMaxGroups;
     a.bdone = arrive + 2 * kMaxGroups;
+    a.that = reinterpret_cast<unsigned long long*>(ds.base + kOffThat);
+    a.spec = 1;
+    a.exc_w = 0;   // no exception lists here: a first-pass mask counts only when exact as written
     a.ghist = reinterpret_cast<int*>(ds.base + kOffGhist);
     a.bq = reinterpret_cast<unsigned long long*>(ds.base + kOffQueue);
     a.t_out = d_t;

@@ -181,12 +181,12 @@ __device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, flo
     // ---- 2. each thread takes a contiguous run of at most 8 entries
     const int per = (M + kSearchThreads - 1) / kSearchThreads;
     const int j0 = min(tid * per, M), j1 = min(j0 + per, M);
-    const F2 LN = shannon ? F2{0.f, 0.f} : df_log2_count((unsigned)N, T);
+    const F2 LN = shannon ? F2{0.f, 0.f} : df_log2_count<false>((unsigned)N, T);
     long long c = 0;
     F2 w{0.f, 0.f};
     for (int j = j0; j < j1; ++j) {
         const int cnt = sIC[j].y;
-        const F2 tk = shannon ? df_hlog2h((unsigned)cnt, T) : df_pow_ratio((unsigned)cnt, LN, q, T);
+        const F2 tk = shannon ? df_hlog2h<false>((unsigned)cnt, T) : df_pow_ratio<false>((unsigned)cnt, LN, q, T);
         sT[j] = make_float2(tk.hi, tk.lo);
         c += cnt;
         w = f2_add(w, tk);
@@ -259,7 +259,7 @@ __device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, flo
                         e = shannon_err(ua, va, ub, vb, fb2);
                     } else {
                         // class powers scaled like the terms (2^64)
-                        const float ab = (qa / class_pow_f32(na, fN, LN, q, T)) * (qb / class_pow_f32(nb, fN, LN, q, T));
+                        const float ab = (qa / class_pow_f32<false>(na, fN, LN, q, T)) * (qb / class_pow_f32<false>(nb, fN, LN, q, T));
                         f = (1.0f - ab) / (q - 1.0f);
                         e = tsallis_err(ab, f, q);
                     }
@@ -325,12 +325,12 @@ __device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, flo
             const long long nb = N - na;
             double f;
             if (shannon) {
-                const double la = df_to_double(df_log2_count((unsigned)na, T));
-                const double lb = df_to_double(df_log2_count((unsigned)nb, T));
+                const double la = df_to_double(df_log2_count<false>((unsigned)na, T));
+                const double lb = df_to_double(df_log2_count<false>((unsigned)nb, T));
                 f = 0.6931471805599453 * ((la - df_to_double(sA) / (double)na) + (lb - df_to_double(sB) / (double)nb));
             } else {
-                const double pa = df_to_double(df_pow_ratio((unsigned)na, LN, q, T));
-                const double pb = df_to_double(df_pow_ratio((unsigned)nb, LN, q, T));
+                const double pa = df_to_double(df_pow_ratio<false>((unsigned)na, LN, q, T));
+                const double pb = df_to_double(df_pow_ratio<false>((unsigned)nb, LN, q, T));
                 const double ab = (df_to_double(sA) / pa) * (df_to_double(sB) / pb);
                 f = (1.0 - ab) / ((double)q - 1.0);
             }

@@ -29,6 +29,7 @@ namespace tsl {
 
 constexpr int kSegThreads = kSearchThreads;  // 512
 constexpr int kSegMinBlocks = 2;
+constexpr int kExcSmem = kMaxBins * 2;   // a tile's exceptions held in shared memory (in the search's sT)
 
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 
@@ -72,32 +73,6 @@ __device__ __forceinline__ void hist8(uint4 r, unsigned LO2, unsigned HI2, int* 
 
 __device__ __forceinline__ int clamp_level(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// n voxels at src into the block histogram.
-__device__ void hist_tile(const int16_t* __restrict__ src, long long n, int lo, int hi, int* shb,
-                          unsigned long long pol) {
-    const int tid = threadIdx.x;
-    const unsigned LO2 = ((unsigned)lo & 0xffffu) * 0x10001u;
-    const unsigned HI2 = ((unsigned)hi & 0xffffu) * 0x10001u;
-    const int head = (int)lmin(n, ((16 - ((uintptr_t)src & 15)) & 15) >> 1);
-    if (tid < head) atomicAdd(shb + clamp_level(src[tid], lo, hi), 1);
-    const uint4* v = reinterpret_cast<const uint4*>(src + head);
-    const long long nv = (n - head) >> 3;
-    long long i = tid;
-    for (; i + 3 * kSegThreads < nv; i += 4 * kSegThreads) {
-        const uint4 r0 = ld_v4_policy(v + i, pol);
-        const uint4 r1 = ld_v4_policy(v + i + kSegThreads, pol);
-        const uint4 r2 = ld_v4_policy(v + i + 2 * kSegThreads, pol);
-        const uint4 r3 = ld_v4_policy(v + i + 3 * kSegThreads, pol);
-        hist8(r0, LO2, HI2, shb);
-        hist8(r1, LO2, HI2, shb);
-        hist8(r2, LO2, HI2, shb);
-        hist8(r3, LO2, HI2, shb);
-    }
-    for (; i < nv; i += kSegThreads) hist8(ld_v4_policy(v + i, pol), LO2, HI2, shb);
-    const long long t0 = head + (nv << 3);
-    if (t0 + tid < n) atomicAdd(shb + clamp_level(src[t0 + tid], lo, hi), 1);
-}
-
 // Algorithm 1 on 8 voxels with packed 16x2 compares: byte = 1 where
 // v <= T (le) or v > T (!le).
 __device__ __forceinline__ uint2 mask8(uint4 r, unsigned T2, bool le) {
@@ -118,6 +93,120 @@ __device__ __forceinline__ uint2 mask8(uint4 r, unsigned T2, bool le) {
 __device__ __forceinline__ int bin_threshold(int t, int lo, int L, int shift) {
     const int T = (t >= ((L - 1) >> shift)) ? 32767 : lo + ((t + 1) << shift) - 1;
     return T > 32767 ? 32767 : T;
+}
+
+// First-pass exceptions: voxels whose (clamped) value lies in [wlo, whi],
+// the window of levels around the predicted threshold, are appended to a
+// shared-memory list as (position in group << 12) | (level - wbase).
+struct ExcCtx {
+    unsigned* list;     // shared memory
+    int* n;             // shared counter
+    int cap;
+    unsigned wlo2, whi2;   // window bounds as packed 16x2 values
+    int wlo, whi;
+    int lo;             // value of level 0
+    int wbase;          // level stored as 0
+    long long pos0;     // position in the group of src[0]
+};
+
+__device__ __forceinline__ void exc_append1(const ExcCtx& e, long long pos, int c) {
+    if (c >= e.wlo && c <= e.whi) {
+        const int k = atomicAdd(e.n, 1);
+        if (k < e.cap) e.list[k] = ((unsigned)pos << 12) | (unsigned)(c - e.lo - e.wbase);
+    }
+}
+
+// The exceptions among 8 clamped voxels (4 packed words) at group position pos.
+__device__ __forceinline__ void exc_append8(const ExcCtx& e, const unsigned (&cl)[4], long long pos) {
+    unsigned bits = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const unsigned m = __vcmpges2(cl[j], e.wlo2) & __vcmples2(cl[j], e.whi2);
+        bits |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * j);
+    }
+    if (bits == 0) return;
+    int k = atomicAdd(e.n, __popc(bits));
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const unsigned w = cl[b >> 1];
+        const int c = (b & 1) ? ((int)w >> 16) : (int)(short)(w & 0xffffu);
+        if (k < e.cap) e.list[k] = ((unsigned)(pos + b) << 12) | (unsigned)(c - e.lo - e.wbase);
+        ++k;
+    }
+}
+
+// Histogram of 8 voxels that also returns the clamped words (for the
+// exception test).
+__device__ __forceinline__ void hist8c(uint4 r, unsigned LO2, unsigned HI2, int* shb, unsigned (&cl)[4]) {
+    const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const unsigned c = __vmins2(__vmaxs2(w[j], LO2), HI2);
+        cl[j] = c;
+        atomicAdd(shb + (int)(short)(c & 0xffffu), 1);
+        atomicAdd(shb + (((int)c) >> 16), 1);
+    }
+}
+
+// n voxels at src into the block histogram. kBin: Algorithm 1 is applied in
+// the same pass with a predicted threshold (mask8 below), writing dst; kExc:
+// the voxels near that threshold are also listed (ExcCtx).
+template <bool kBin, bool kExc>
+__device__ void hist_tile(const int16_t* __restrict__ src, long long n, int lo, int hi, int* shb,
+                          unsigned long long pol, uint8_t* __restrict__ dst, unsigned T2, bool le, int T,
+                          const ExcCtx& ex) {
+    const int tid = threadIdx.x;
+    const unsigned LO2 = ((unsigned)lo & 0xffffu) * 0x10001u;
+    const unsigned HI2 = ((unsigned)hi & 0xffffu) * 0x10001u;
+    const int head = (int)lmin(n, ((16 - ((uintptr_t)src & 15)) & 15) >> 1);
+    if (tid < head) {
+        const int x = src[tid];
+        const int c = clamp_level(x, lo, hi);
+        atomicAdd(shb + c, 1);
+        if (kBin) dst[tid] = (uint8_t)(((x <= T) == le) ? 1 : 0);
+        if (kExc) exc_append1(ex, ex.pos0 + tid, c);
+    }
+    const uint4* v = reinterpret_cast<const uint4*>(src + head);
+    uint8_t* d = dst + head;
+    const long long nv = (n - head) >> 3;
+    const long long p0 = ex.pos0 + head;
+    long long i = tid;
+    unsigned cl[4];
+    for (; i + 3 * kSegThreads < nv; i += 4 * kSegThreads) {
+        const uint4 r0 = ld_v4_policy(v + i, pol);
+        const uint4 r1 = ld_v4_policy(v + i + kSegThreads, pol);
+        const uint4 r2 = ld_v4_policy(v + i + 2 * kSegThreads, pol);
+        const uint4 r3 = ld_v4_policy(v + i + 3 * kSegThreads, pol);
+        if (kBin) {
+            st_stream(d + i * 8, mask8(r0, T2, le));
+            st_stream(d + (i + kSegThreads) * 8, mask8(r1, T2, le));
+            st_stream(d + (i + 2 * kSegThreads) * 8, mask8(r2, T2, le));
+            st_stream(d + (i + 3 * kSegThreads) * 8, mask8(r3, T2, le));
+        }
+        hist8c(r0, LO2, HI2, shb, cl);
+        if (kExc) exc_append8(ex, cl, p0 + i * 8);
+        hist8c(r1, LO2, HI2, shb, cl);
+        if (kExc) exc_append8(ex, cl, p0 + (i + kSegThreads) * 8);
+        hist8c(r2, LO2, HI2, shb, cl);
+        if (kExc) exc_append8(ex, cl, p0 + (i + 2 * kSegThreads) * 8);
+        hist8c(r3, LO2, HI2, shb, cl);
+        if (kExc) exc_append8(ex, cl, p0 + (i + 3 * kSegThreads) * 8);
+    }
+    for (; i < nv; i += kSegThreads) {
+        const uint4 r = ld_v4_policy(v + i, pol);
+        if (kBin) st_stream(d + i * 8, mask8(r, T2, le));
+        hist8c(r, LO2, HI2, shb, cl);
+        if (kExc) exc_append8(ex, cl, p0 + i * 8);
+    }
+    const long long t0 = head + (nv << 3);
+    if (t0 + tid < n) {
+        const int x = src[t0 + tid];
+        const int c = clamp_level(x, lo, hi);
+        atomicAdd(shb + c, 1);
+        if (kBin) dst[t0 + tid] = (uint8_t)(((x <= T) == le) ? 1 : 0);
+        if (kExc) exc_append1(ex, ex.pos0 + t0 + tid, c);
+    }
 }
 
 // Algorithm 1 over n voxels. t < 0 (no valid threshold) writes zeros.
@@ -156,7 +245,8 @@ struct Work {
     int kind;   // 0 none, 1 histogram, 2 binarise
     int group;
     int tile;
-    int t;      // binarise threshold (-2: its wait ran out, skip)
+    int t;      // binarise: threshold (-2: its wait ran out, skip); histogram:
+                // predicted threshold to binarise with in the same pass (-1: none)
 };
 
 __device__ __forceinline__ int group_tiles(const SegArgs& a, int g) {
@@ -195,6 +285,27 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
+// Predicted threshold of group g for this launch: the first histogram tile
+// of the group to be scheduled fixes it (compare-and-swap on the group's
+// slot) to the threshold found most recently in this launch, or to -1 (no
+// prediction, the first pass only counts) when none is found yet. Values
+// carry the launch tag, so nothing from an earlier launch is used.
+__device__ __forceinline__ int group_hint(const SegArgs& a, int epoch, int g) {
+    const unsigned long long tag = (unsigned long long)(unsigned)(epoch + 1) << 32;
+    const unsigned long long hmask = 0xffffffff00000000ull;
+    const unsigned long long cur = *(volatile unsigned long long*)&a.hdr->latest;
+    const int t = (cur & hmask) == tag ? (int)(cur & 0xffffffffu) - 1 : -1;
+    unsigned long long old = *(volatile unsigned long long*)&a.that[g];
+    if ((old & hmask) != tag) {
+        const unsigned long long prev = atomicCAS(&a.that[g], old, tag | (unsigned)(t + 1));
+        if (prev == old) return t;
+        old = prev;
+    }
+    return (old & hmask) == tag ? (int)(old & 0xffffffffu) - 1 : -1;
+}
+
+constexpr int kNoopTile = 0xfffff;   // queue entry of a group whose first-pass mask is exact
+
 // Per-block scheduler state (lane 0 of the scheduler warp).
 struct SchedState {
     long long pend;   // claimed binarise queue position not yet published (-1: none)
@@ -218,7 +329,7 @@ __device__ Work next_work(const SegArgs& a, int epoch, SchedState& st) {
     ScratchHeader* h = a.hdr;
     if (a.phases == kPhaseHist) {
         const unsigned k = atomicAdd(&h->h_next, 1u);
-        if (k < a.ntotal) { w.kind = 1; locate(a, k, w.group, w.tile); }
+        if (k < a.ntotal) { w.kind = 1; locate(a, k, w.group, w.tile); w.t = -1; }
         return w;
     }
     if (a.phases == kPhaseBin) {
@@ -236,6 +347,10 @@ __device__ Work next_work(const SegArgs& a, int epoch, SchedState& st) {
         if (st.pend >= 0) {
             const unsigned long long e = ld_acquire_u64(&a.bq[st.pend]);
             if (bq_valid(e, epoch)) {
+                if ((int)(e & 0xfffff) == kNoopTile) {   // nothing to re-binarise
+                    st.pend = -1;
+                    continue;
+                }
                 w.kind = 2;
                 w.group = (int)((e >> 20) & 0xfffff);
                 w.tile = (int)(e & 0xfffff);
@@ -253,6 +368,7 @@ __device__ Work next_work(const SegArgs& a, int epoch, SchedState& st) {
             if (k < a.ntotal) {
                 w.kind = 1;
                 locate(a, k, w.group, w.tile);
+                w.t = -1;   // the prediction is fixed when the tile starts (workers)
                 st.b_turn = true;
                 return w;
             }
@@ -305,10 +421,14 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
     __shared__ SearchSmem ssm;
     __shared__ Work s_work[2];
     __shared__ int s_last;
+    __shared__ int s_any;
+    __shared__ int s_exc_n, s_exc_cnt, s_exc_base, s_hint;
+    unsigned* sexc = reinterpret_cast<unsigned*>(sT);   // a tile's exceptions (the search's scratch is free then)
     const int tid = threadIdx.x;
     const int epoch = *(volatile int*)&a.hdr->epoch;
 
     for (int i = tid; i < kMaxBins; i += kBlockThreads) sh[i] = 0;
+    if (tid == 0) s_exc_n = 0;
     __syncthreads();
 
     if (tid >= kSegThreads) {
@@ -329,7 +449,7 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
         const unsigned long long pol_drop = policy_evict_first();
         for (int i = 0;; ++i) {
             handoff_sync();
-            const Work w = s_work[i & 1];
+            Work w = s_work[i & 1];
             if (w.kind == 0) break;
             const int16_t* gvol;
             uint8_t* gmask;
@@ -344,9 +464,55 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
             }
             const long long off = (long long)w.tile * a.tile_vox;
             const long long n = lmin((long long)a.tile_vox, gn - off);
-            if (w.kind == 1) {
-                hist_tile(gvol + off, n, a.lo, hi, shb, pol_keep);
+            if (w.kind == 1 && a.spec) {
+                // the group's predicted threshold, fixed by its first tile to start
+                if (tid == 0) s_hint = group_hint(a, epoch, w.group);
                 work_sync();
+                w.t = s_hint;
+            }
+            if (w.kind == 1) {
+                ExcCtx ex;
+                ex.pos0 = off;
+                const bool with_exc = w.t >= 0 && a.exc_w > 0;
+                if (w.t >= 0) {
+                    const int T = bin_threshold(w.t, a.lo, a.L, 0);
+                    const unsigned T2 = ((unsigned)T & 0xffffu) * 0x10001u;
+                    if (with_exc) {
+                        ex.list = sexc;
+                        ex.n = &s_exc_n;
+                        ex.cap = kExcSmem;
+                        ex.lo = a.lo;
+                        ex.wbase = w.t - a.exc_w + 1;
+                        const int wl = a.lo + ex.wbase, wh = a.lo + w.t + a.exc_w;   // window as values
+                        ex.wlo = wl < a.lo ? a.lo : wl;
+                        ex.whi = wh > hi ? hi : wh;
+                        ex.wlo2 = ((unsigned)ex.wlo & 0xffffu) * 0x10001u;
+                        ex.whi2 = ((unsigned)ex.whi & 0xffffu) * 0x10001u;
+                        hist_tile<true, true>(gvol + off, n, a.lo, hi, shb, pol_keep, gmask + off, T2,
+                                              a.polarity == 0, T, ex);
+                    } else {
+                        hist_tile<true, false>(gvol + off, n, a.lo, hi, shb, pol_keep, gmask + off, T2,
+                                               a.polarity == 0, T, ex);
+                    }
+                } else {
+                    hist_tile<false, false>(gvol + off, n, a.lo, hi, shb, pol_keep, nullptr, 0u, true, 0, ex);
+                }
+                work_sync();
+                if (with_exc) {
+                    // this tile's exceptions into the group's list
+                    if (tid == 0) {
+                        const int ne = s_exc_n;
+                        s_exc_n = 0;
+                        s_exc_cnt = ne;
+                        s_exc_base = ne > kExcSmem ? atomicAdd(&a.exc_n[w.group], a.exc_cap + 1)   // overflow
+                                                   : atomicAdd(&a.exc_n[w.group], ne);
+                    }
+                    work_sync();
+                    const int ne = s_exc_cnt, eb = s_exc_base;
+                    unsigned* gl = a.exc + (long long)w.group * a.exc_cap;
+                    if (ne <= kExcSmem)
+                        for (int k = tid; k < ne && eb + k < a.exc_cap; k += kSegThreads) gl[eb + k] = sexc[k];
+                }
                 // add the block histogram to the group's, leave sh zeroed
                 int* gh = a.ghist + (long long)w.group * a.L;
                 for (int b = tid; b < a.L; b += kSegThreads) {
@@ -370,23 +536,66 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                         SearchResult r = search1d_block<WorkSync>(
                             gh, a.L, a.q, a.curve ? a.curve + (long long)w.group * (a.L - 1) : nullptr, ssm, sT,
                             sIC, dft);
+                        // the first pass binarised with a predicted threshold t^:
+                        // its mask is exact when no voxel has a level between
+                        // t^ and t (no voxel changes side)
+                        bool exact = false;
+                        if (a.spec) {
+                            const unsigned long long hv = *(volatile unsigned long long*)&a.that[w.group];
+                            const int th = (hv >> 32) == (unsigned long long)(unsigned)(epoch + 1)
+                                               ? (int)(hv & 0xffffffffu) - 1 : -1;
+                            if (th >= 0 && r.t >= 0) {
+                                const int b0 = (th < r.t ? th : r.t) + 1, b1 = th < r.t ? r.t : th;
+                                int any = 0;
+                                for (int b = b0 + tid; b <= b1; b += kSegThreads) any |= __ldcg(gh + b);
+                                if (tid == 0) s_any = 0;
+                                work_sync();
+                                if (any) s_any = 1;
+                                work_sync();
+                                exact = s_any == 0;
+                                const int ne = a.exc_w > 0 ? *(volatile int*)&a.exc_n[w.group] : 0;
+                                const int dt = r.t - th;
+                                if (!exact && a.exc_w > 0 && dt >= -a.exc_w && dt <= a.exc_w && ne <= a.exc_cap) {
+                                    // every voxel that changes side has a level in
+                                    // (b0 - 1, b1], inside the window: it is listed,
+                                    // so Algorithm 1 at t is applied to those voxels
+                                    const unsigned* gl = a.exc + (long long)w.group * a.exc_cap;
+                                    const int wbase = th - a.exc_w + 1;
+                                    const bool le = a.polarity == 0;
+                                    for (int k = tid; k < ne; k += kSegThreads) {
+                                        const unsigned e = __ldcg(gl + k);
+                                        const int lev = (int)(e & 0xfffu) + wbase;
+                                        if (lev >= b0 && lev <= b1) gmask[e >> 12] = ((lev <= r.t) == le) ? 1 : 0;
+                                    }
+                                    exact = true;
+                                }
+                            }
+                        }
                         for (int b = tid; b < a.L; b += kSegThreads) gh[b] = 0;   // scratch left zeroed
                         const int nt = group_tiles(a, w.group);
                         if (tid == 0) {
                             a.t_out[w.group] = r.t;
                             a.phi_out[w.group] = r.phi;
-                            a.status[w.group] = r.status;
+                            a.status[w.group] = r.status | (exact ? TSALLIS_STATUS_FIRST_PASS_EXACT : 0);
                             a.arrive[w.group] = 0;
+                            if (a.exc_w > 0) a.exc_n[w.group] = 0;
                             a.done_flag[w.group] = epoch + 1;
+                            if (exact) atomicAdd(&a.bdone[w.group], nt);
+                            if (r.t >= 0)
+                                *(volatile unsigned long long*)&a.hdr->latest =
+                                    ((unsigned long long)(unsigned)(epoch + 1) << 32) | (unsigned)(r.t + 1);
                             __threadfence();
                             s_last = (int)atomicAdd(&a.hdr->b_tail, (unsigned)nt);
                         }
                         work_sync();
                         // the group's binarise tiles enter the queue, most
-                        // recently read tile first
+                        // recently read tile first (no-op entries when the
+                        // first-pass mask is exact: the queue length stays
+                        // the number of tiles, which is how blocks know when
+                        // all work is done)
                         const int base = s_last;
                         for (int j = tid; j < nt; j += kSegThreads)
-                            st_release_u64(&a.bq[base + j], bq_pack(epoch, w.group, nt - 1 - j));
+                            st_release_u64(&a.bq[base + j], bq_pack(epoch, w.group, exact ? kNoopTile : nt - 1 - j));
                     }
                 }
             } else if (w.t != -2) {
@@ -418,7 +627,10 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                     a.status[g] = 5; /* TSALLIS_ERR_TIMEOUT */
                 }
                 a.bdone[g] = 0;
-                if (err) a.arrive[g] = 0;
+                if (err) {
+                    a.arrive[g] = 0;
+                    if (a.exc_w > 0) a.exc_n[g] = 0;
+                }
             }
             if (err) {
                 // clear every group's histogram
@@ -467,7 +679,7 @@ __global__ void k_probe_dfmath(const unsigned* __restrict__ h, long long n, unsi
     const F2 LN = df_log2_u32(N, T);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const unsigned x = h[i];
-        pw[i] = (x >= 1u && x <= N) ? df_to_double(df_pow_ratio(x, LN, q, T)) * 0x1p-64 : 0.0;
+        pw[i] = (x >= 1u && x <= N) ? df_to_double(df_pow_ratio<true>(x, LN, q, T)) * 0x1p-64 : 0.0;
         lg[i] = x >= 1u ? df_to_double(df_log2_u32(x, T)) : 0.0;
     }
 }

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_rows(const S2Args a) {
     const long long o = s2_off(a, k) + (long long)i * a.L2;
     const int h = s < a.L2 ? __ldg(a.hist + o + s) : 0;
     F2 w{0.f, 0.f};
-    if (h > 0) w = a.q == 1.0f ? df_hlog2h((unsigned)h, a.T) : df_pow_ratio((unsigned)h, F2{kFixedLog2N, 0.f}, a.q, a.T);
+    if (h > 0) w = a.q == 1.0f ? df_hlog2h<true>((unsigned)h, a.T) : df_pow_ratio<true>((unsigned)h, F2{kFixedLog2N, 0.f}, a.q, a.T);
     int c;
     F2 ws;
     block_scan(h, w, false, sm, c, ws);
@@ -377,7 +377,7 @@ __device__ __forceinline__ void eval32(const Quad& u, float q, const DfTables* T
     } else {
         const F2 LN{kFixedLog2N, 0.f};
         const float fN = 2147483648.0f;
-        const float ab = (qa / class_pow_f32(u.na, fN, LN, q, T)) * (qb / class_pow_f32(u.nb, fN, LN, q, T));
+        const float ab = (qa / class_pow_f32<true>(u.na, fN, LN, q, T)) * (qb / class_pow_f32<true>(u.nb, fN, LN, q, T));
         f = (1.0f - ab) / (q - 1.0f);
         err = tsallis_err(ab, f, q);
     }
@@ -385,14 +385,14 @@ __device__ __forceinline__ void eval32(const Quad& u, float q, const DfTables* T
 
 __device__ __forceinline__ double eval64(const Quad& u, float q, const DfTables* T) {
     if (q == 1.0f) {
-        const double la = df_to_double(df_log2_count((unsigned)u.na, T));
-        const double lb = df_to_double(df_log2_count((unsigned)u.nb, T));
+        const double la = df_to_double(df_log2_count<true>((unsigned)u.na, T));
+        const double lb = df_to_double(df_log2_count<true>((unsigned)u.nb, T));
         return 0.6931471805599453 *
                ((la - df_to_double(u.qa) / (double)u.na) + (lb - df_to_double(u.qb) / (double)u.nb));
     }
     const F2 LN{kFixedLog2N, 0.f};
-    const double pa = df_to_double(df_pow_ratio((unsigned)u.na, LN, q, T));
-    const double pb = df_to_double(df_pow_ratio((unsigned)u.nb, LN, q, T));
+    const double pa = df_to_double(df_pow_ratio<true>((unsigned)u.na, LN, q, T));
+    const double pb = df_to_double(df_pow_ratio<true>((unsigned)u.nb, LN, q, T));
     const double ab = (df_to_double(u.qa) / pa) * (df_to_double(u.qb) / pb);
     return (1.0 - ab) / ((double)q - 1.0);
 }

@@ -240,15 +240,22 @@ def test_segment_ragged_shapes(shape, mode):
     _check_step(v, mode, 0.8, polarity="high")
 
 
+def _same(outs, ref):
+    """Equal masks, thresholds, values and statuses. The first-pass bit of a
+    status depends on which searches finished first, so it is not compared."""
+    for i, (a, b) in enumerate(zip(outs, ref)):
+        if i == 3:
+            a, b = a & ~tg.TSALLIS_STATUS_FIRST_PASS_EXACT, b & ~tg.TSALLIS_STATUS_FIRST_PASS_EXACT
+        assert torch.equal(a, b), i
+
+
 def test_segment_repeated_calls_and_graph_replay():
     v = phantom.generate_host(phantom.chest_volume(7, nz=40))
     dv = _cuda(v)
     p = tg.tsallis_params(q=0.8)
     ref = [x.clone() for x in tg.tsallis_segment(dv, p)]
     for _ in range(3):
-        out = tg.tsallis_segment(dv, p)
-        for a, b in zip(out, ref):
-            assert torch.equal(a, b)
+        _same(tg.tsallis_segment(dv, p), ref)
     mask = torch.empty_like(ref[0])
     t = torch.empty_like(ref[1])
     phi = torch.empty_like(ref[2])
@@ -266,8 +273,7 @@ def test_segment_repeated_calls_and_graph_replay():
         t.fill_(-7)
         g.replay()
         torch.cuda.synchronize()
-        for a, b in zip((mask, t, phi, st), ref):
-            assert torch.equal(a, b)
+        _same((mask, t, phi, st), ref)
 
 
 def test_wait_timeout_reports_status_and_context_recovers():
