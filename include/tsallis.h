@@ -219,12 +219,34 @@ typedef struct {
  * Steps 1-4 for nvol volumes of uneven depth in one persistent launch, one
  * histogram and threshold per volume (whole-volume mode) or per slice
  * (per-slice mode, slices of all volumes numbered consecutively).
- *   h_vols   host array of nvol descriptors (read during the call only).
- *   d_t, d_phi, d_status  out, one entry per histogram.
+ *   h_vols   host array of nvol descriptors (read during the call only);
+ *            each volume and mask 16-byte aligned, nz >= 1.
+ *   d_t, d_phi, d_status  out, one entry per histogram, in volume order.
+ * The volumes' group table is written on the device by a small kernel
+ * whose arguments carry the descriptors, so the whole call (two or more
+ * launches, no host copies) can be captured in a CUDA graph once a first
+ * call has sized the context's scratch. Per histogram at most 2^31 - 1
+ * voxels; in all at most 2^20 - 2 histograms. The 2-D form runs volume by
+ * volume. Errors as for tsallis_segment.
  */
 tsallis_status tsallis_segment_batch(tsallis_ctx* ctx, const tsallis_volume* h_vols, int32_t nvol,
                                      const tsallis_params* p, int32_t* d_t, float* d_phi, int32_t* d_status,
                                      cudaStream_t stream);
+
+/*
+ * Autotuner for tsallis_segment_batch (the counterpart of the paper's
+ * grid/block-size experiment, Table 4): runs the batch with every work-tile
+ * size in {16384, 32768, 65536, 131072, 262144} voxels and every resident
+ * block count per SM the kernel allows, timing the best of three passes
+ * each, and keeps the fastest as the context's launch shape (see
+ * tsallis_set_launch_shape). Synchronous; the outputs hold the last pass's
+ * results. The chosen shape and time go to *tile_vox, *blocks_per_sm and
+ * *best_ms (each may be NULL). 1-D form only.
+ */
+tsallis_status tsallis_autotune_batch(tsallis_ctx* ctx, const tsallis_volume* h_vols, int32_t nvol,
+                                      const tsallis_params* p, int32_t* d_t, float* d_phi, int32_t* d_status,
+                                      cudaStream_t stream, int32_t* tile_vox, int32_t* blocks_per_sm,
+                                      float* best_ms);
 
 /*
  * tsallis_segment_static: tsallis_segment for callers that cannot allocate

@@ -85,6 +85,9 @@ _SIGS = {
     "tsallis_segment": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
     "tsallis_segment_batch": ([_P, ctypes.POINTER(Volume), ctypes.c_int32, ctypes.POINTER(Params), _P, _P, _P, _P],
                               ctypes.c_int),
+    "tsallis_autotune_batch": ([_P, ctypes.POINTER(Volume), ctypes.c_int32, ctypes.POINTER(Params), _P, _P, _P, _P,
+                                ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
     "tsallis_probe_dfmath": ([_P, _P, _I64, ctypes.c_uint32, ctypes.c_float, _P, _P, _P], ctypes.c_int),
 }
 
@@ -282,9 +285,7 @@ def tsallis_segment(vol: torch.Tensor, p: Params | None = None, mask: torch.Tens
     return mask, t, phi, status
 
 
-def tsallis_segment_batch(vols, p: Params | None = None, masks=None):
-    """Steps 1-4 for a list of volumes in one launch: (masks, t, phi, status)."""
-    p = p or tsallis_params()
+def _batch_args(vols, p, masks, outs):
     vols = list(vols)
     if not vols:
         raise ValueError("empty batch")
@@ -294,13 +295,41 @@ def tsallis_segment_batch(vols, p: Params | None = None, masks=None):
     arr = (Volume * len(vols))()
     nh = 0
     for i, (v, m) in enumerate(zip(vols, masks)):
+        if v.device != dev or m.device != dev or m.dtype != torch.uint8 or m.shape != v.shape:
+            raise ValueError("volume %d: mask must be a uint8 tensor of the volume's shape on its device" % i)
         nx, ny, nz = _vol3(v)
+        if not m.is_contiguous():
+            raise ValueError("mask %d must be contiguous" % i)
         arr[i] = Volume(v.data_ptr(), m.data_ptr(), nx, ny, nz)
         nh += _nh(p, nz)
-    t = torch.empty((nh, 2) if p.two_d else (nh,), dtype=torch.int32, device=dev)
-    phi = torch.empty(nh, dtype=torch.float32, device=dev)
-    st = torch.empty(nh, dtype=torch.int32, device=dev)
-    _check("tsallis_segment_batch", lib().tsallis_segment_batch(context(dev), arr, len(vols), ctypes.byref(p),
-                                                                t.data_ptr(), phi.data_ptr(), st.data_ptr(),
-                                                                _stream(vols[0])))
+    if outs is None:
+        t = torch.empty((nh, 2) if p.two_d else (nh,), dtype=torch.int32, device=dev)
+        phi = torch.empty(nh, dtype=torch.float32, device=dev)
+        st = torch.empty(nh, dtype=torch.int32, device=dev)
+    else:
+        t, phi, st = outs
+    return vols, masks, arr, t, phi, st
+
+
+def tsallis_segment_batch(vols, p: Params | None = None, masks=None, outs=None):
+    """Steps 1-4 for a list of volumes in one persistent launch:
+    (masks, t, phi, status), one threshold per volume (whole-volume mode) or
+    per slice (per-slice mode, slices numbered across the batch)."""
+    p = p or tsallis_params()
+    vols, masks, arr, t, phi, st = _batch_args(vols, p, masks, outs)
+    _check("tsallis_segment_batch", lib().tsallis_segment_batch(context(vols[0].device), arr, len(vols),
+                                                                ctypes.byref(p), t.data_ptr(), phi.data_ptr(),
+                                                                st.data_ptr(), _stream(vols[0])))
     return masks, t, phi, st
+
+
+def tsallis_autotune_batch(vols, p: Params | None = None, masks=None, outs=None):
+    """Times the batch over the launch shapes and keeps the fastest for the
+    context: returns (tile_vox, blocks_per_sm, best_ms)."""
+    p = p or tsallis_params()
+    vols, masks, arr, t, phi, st = _batch_args(vols, p, masks, outs)
+    tv, bps, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check("tsallis_autotune_batch", lib().tsallis_autotune_batch(
+        context(vols[0].device), arr, len(vols), ctypes.byref(p), t.data_ptr(), phi.data_ptr(), st.data_ptr(),
+        _stream(vols[0]), ctypes.byref(tv), ctypes.byref(bps), ctypes.byref(ms)))
+    return tv.value, bps.value, ms.value

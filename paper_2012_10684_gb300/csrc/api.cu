@@ -612,11 +612,164 @@ tsallis_status tsallis_probe_dfmath(tsallis_ctx* c, const uint32_t* d_h, int64_t
 tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vols, int32_t nvol,
                                      const tsallis_params* p, int32_t* d_t, float* d_phi, int32_t* d_status,
                                      cudaStream_t stream) {
-    (void)h_vols; (void)nvol; (void)d_t; (void)d_phi; (void)d_status; (void)stream;
+    tsallis_status st = check_params(p);
+    if (st != TSALLIS_OK) return st;
+    if (!c || nvol < 0) return TSALLIS_ERR_INVALID_ARG;
+    if (nvol == 0) return TSALLIS_OK;
+    if (!h_vols || !d_t || !d_phi || !d_status) return TSALLIS_ERR_INVALID_ARG;
+    // validate every volume and lay out its groups and tiles
+    std::vector<BatchVolDesc> vd((size_t)nvol);
+    long long ng = 0, ntot = 0;
+    for (int i = 0; i < nvol; ++i) {
+        const tsallis_volume& v = h_vols[i];
+        if ((st = check_shape(v.nx, v.ny, v.nz)) != TSALLIS_OK) return st;
+        if (v.nz == 0) return TSALLIS_ERR_INVALID_ARG;
+        if (!v.vol || !v.mask) return TSALLIS_ERR_INVALID_ARG;
+        if (!aligned16(v.vol) || !aligned16(v.mask)) return TSALLIS_ERR_ALIGNMENT;
+        const long long slice = v.nx * v.ny;
+        const long long gvox = p->mode == TSALLIS_PER_SLICE ? slice : slice * v.nz;
+        const long long gv = p->mode == TSALLIS_PER_SLICE ? v.nz : 1;
+        if (gvox > (1ll << 31) - 1) return TSALLIS_ERR_INVALID_ARG;
+        const long long nt = (gvox + c->tile_vox - 1) / c->tile_vox;
+        vd[i] = BatchVolDesc{v.vol, v.mask, gvox, (int)gv, (int)nt, (int)ng, (int)ntot};
+        ng += gv;
+        ntot += gv * nt;
+        // group and tile numbers must fit the work-queue entries (20 bits each)
+        if (ng >= (1 << 20) - 1 || nt >= (1 << 20) - 1 || ntot > 0x7fffffffll) return TSALLIS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    if (p->two_d) {
+        // the 2-D form runs volume by volume (its kernels take one volume)
+        long long h = 0;
+        for (int i = 0; i < nvol; ++i) {
+            const tsallis_volume& v = h_vols[i];
+            const long long gv = vd[i].ngroups;
+            if ((st = segment2d(c, v.vol, v.nx, v.ny, v.nz, p, gv, vd[i].gvox, v.mask, d_t + 2 * h, d_phi + h,
+                                d_status + h, stream)) != TSALLIS_OK)
+                return st;
+            h += gv;
+        }
+        return TSALLIS_OK;
+    }
+    if ((st = ensure_scratch(c, ng, ntot)) != TSALLIS_OK) return st;
+    // the group table, written on the device (capturable in a CUDA graph)
+    const size_t table = (size_t)ng * sizeof(GroupDesc);
+    if (!c->batch_buf || c->batch_bytes < table) {
+        size_t cap = c->batch_bytes > 0 ? c->batch_bytes : 4096;
+        while (cap < table) cap *= 2;
+        if (c->batch_buf) {
+            if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
+            cudaFree(c->batch_buf);
+            c->batch_buf = nullptr;
+            c->batch_bytes = 0;
+        }
+        if (cudaMalloc(&c->batch_buf, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return TSALLIS_ERR_OOM;
+        }
+        c->batch_bytes = cap;
+    }
+    GroupDesc* groups = static_cast<GroupDesc*>(c->batch_buf);
+    for (int i0 = 0; i0 < nvol; i0 += kExpandVols) {
+        ExpandArgs ea;
+        std::memset(&ea, 0, sizeof(ea));
+        ea.nvol = nvol - i0 < kExpandVols ? nvol - i0 : kExpandVols;
+        for (int k = 0; k < ea.nvol; ++k) ea.v[k] = vd[(size_t)(i0 + k)];
+        const int gend = i0 + ea.nvol < nvol ? vd[(size_t)(i0 + ea.nvol)].group_off : (int)ng;
+        ea.ngroups = gend - vd[(size_t)i0].group_off;
+        ea.out = groups;
+        if (launch_expand_groups(ea, stream) != cudaSuccess) return TSALLIS_ERR_CUDA;
+    }
+    SegArgs a;
+    fill_common(a, p, c);
+    a.groups = groups;
+    a.ngroups = (int)ng;
+    a.ntotal = (unsigned)ntot;
+    a.phases = kPhaseHist | kPhaseSearch | kPhaseBin;
+    ScratchView sv = view(c);
+    a.hdr = sv.hdr;
+    a.arrive = sv.arrive;
+    a.done_flag = sv.done_flag;
+    a.bdone = sv.bdone;
+    a.that = sv.that;
+    a.spec = c->speculate;
+    a.exc = sv.exc;
+    a.exc_n = sv.exc_n;
+    a.exc_cap = kExcCap;
+    bool small = true;
+    for (const BatchVolDesc& v : vd) small = small && v.gvox <= (1ll << 20);
+    a.exc_w = small ? kExcWindow : 0;
+    a.bq = sv.bq;
+    a.ghist = sv.ghist;
+    a.t_out = d_t;
+    a.phi_out = d_phi;
+    a.status = d_status;
+    return cuda_status(launch_segment1d(a, grid_for(c, a.ntotal), c->copies, stream));
+}
+
+tsallis_status tsallis_autotune_batch(tsallis_ctx* c, const tsallis_volume* h_vols, int32_t nvol,
+                                      const tsallis_params* p, int32_t* d_t, float* d_phi, int32_t* d_status,
+                                      cudaStream_t stream, int32_t* tile_vox, int32_t* blocks_per_sm,
+                                      float* best_ms) {
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     tsallis_status st = check_params(p);
     if (st != TSALLIS_OK) return st;
-    return TSALLIS_ERR_UNIMPLEMENTED;
+    if (nvol <= 0 || p->two_d) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    const int tiles[] = {16384, 32768, 65536, 131072, 262144};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (e0) cudaEventDestroy(e0);
+        return TSALLIS_ERR_CUDA;
+    }
+    const int old_tile = c->tile_vox, old_bps = c->blocks_per_sm;
+    float best = 0.f;
+    int bt = old_tile, bb = old_bps;
+    for (int tv : tiles) {
+        for (int bps = 1; bps <= c->max_blocks_per_sm; ++bps) {
+            c->tile_vox = tv;
+            c->blocks_per_sm = bps;
+            // one untimed pass (it also grows the scratch), then the best of three
+            if ((st = tsallis_segment_batch(c, h_vols, nvol, p, d_t, d_phi, d_status, stream)) != TSALLIS_OK) break;
+            float ms_min = 0.f;
+            for (int r = 0; r < 3 && st == TSALLIS_OK; ++r) {
+                float ms = 0.f;
+                if (cudaEventRecord(e0, stream) != cudaSuccess) { st = TSALLIS_ERR_CUDA; break; }
+                if ((st = tsallis_segment_batch(c, h_vols, nvol, p, d_t, d_phi, d_status, stream)) != TSALLIS_OK)
+                    break;
+                if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    st = TSALLIS_ERR_CUDA;
+                    break;
+                }
+                if (r == 0 || ms < ms_min) ms_min = ms;
+            }
+            if (st != TSALLIS_OK) break;
+            if (best == 0.f || ms_min < best) {
+                best = ms_min;
+                bt = tv;
+                bb = bps;
+            }
+        }
+        if (st != TSALLIS_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != TSALLIS_OK) {
+        c->tile_vox = old_tile;
+        c->blocks_per_sm = old_bps;
+        cudaGetLastError();
+        return st;
+    }
+    c->tile_vox = bt;
+    c->blocks_per_sm = bb;
+    if (tile_vox) *tile_vox = bt;
+    if (blocks_per_sm) *blocks_per_sm = bb;
+    if (best_ms) *best_ms = best;
+    return TSALLIS_OK;
 }
 
 }  // extern "C"

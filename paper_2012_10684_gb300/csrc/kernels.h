@@ -78,6 +78,26 @@ struct SegArgs {
     const void* df_tables;  // double-float log2/exp2 tables (device)
 };
 
+// A volume of a batch as the descriptor-expansion kernel receives it: its
+// groups (one per slice, or the whole volume) are consecutive.
+struct BatchVolDesc {
+    const int16_t* vol;
+    uint8_t* mask;
+    long long gvox;         // voxels per group
+    int ngroups;            // groups of this volume
+    int ntiles;             // tiles per group
+    int group_off;          // first group of this volume in the batch
+    int tile_off;           // first histogram work item of this volume
+};
+constexpr int kExpandVols = 48;     // volumes per expansion launch (kernel parameter space)
+struct ExpandArgs {
+    BatchVolDesc v[kExpandVols];
+    int nvol;
+    int ngroups;            // groups of these volumes
+    GroupDesc* out;         // the batch's group table (written from v[0].group_off on)
+};
+cudaError_t launch_expand_groups(const ExpandArgs& a, cudaStream_t s);
+
 // Kernel launchers (seg1d.cu).
 cudaError_t launch_segment1d(const SegArgs& a, int grid, int copies, cudaStream_t s);
 cudaError_t launch_search1d(const int32_t* hist, long long nh, int L, float q, int32_t* t, float* phi,

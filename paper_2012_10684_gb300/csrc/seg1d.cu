@@ -705,6 +705,34 @@ cudaError_t launch_probe_dfmath(const unsigned* h, long long n, unsigned N, floa
     return cudaGetLastError();
 }
 
+// Group table of a batch: one thread per group, volume found by binary
+// search over the volumes' first groups.
+__global__ void k_expand_groups(const ExpandArgs a) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.ngroups) return;
+    const int gg = a.v[0].group_off + g;
+    int lo = 0, hi = a.nvol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.v[mid].group_off <= gg) lo = mid; else hi = mid - 1;
+    }
+    const BatchVolDesc& v = a.v[lo];
+    const int k = gg - v.group_off;
+    GroupDesc d;
+    d.vol = v.vol + (long long)k * v.gvox;
+    d.mask = v.mask + (long long)k * v.gvox;
+    d.nvox = v.gvox;
+    d.ntiles = v.ntiles;
+    d.tile_off = v.tile_off + k * v.ntiles;
+    a.out[gg] = d;
+}
+
+cudaError_t launch_expand_groups(const ExpandArgs& a, cudaStream_t s) {
+    if (a.ngroups <= 0) return cudaSuccess;
+    k_expand_groups<<<(a.ngroups + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 int segment1d_threads() { return kBlockThreads; }
 int segment1d_smem_bytes(int L, int copies) {
     (void)L;
