@@ -39,6 +39,11 @@ struct tsallis_ctx {
     int slice_kernel = TSALLIS_SLICE_KERNEL_AUTO;
     int speculate = 0;            // tile kernel: binarise in the first pass with a predicted threshold
     int cluster_max = 0;
+    // term table of the per-slice search (built for one slice size and q)
+    float2* ptab = nullptr;
+    long long ptab_cap = 0;     // entries allocated
+    long long ptab_n = -1;      // slice size it holds
+    float ptab_q = 0.f;
 };
 
 namespace {
@@ -133,6 +138,39 @@ tsallis_status ensure_scratch(tsallis_ctx* c, long long ngroups, long long ntile
     c->cap_groups = capg;
     c->cap_tiles = capt;
     return TSALLIS_OK;
+}
+
+// The term table for groups of n voxels at q: reused while n and q stay
+// the same, else rebuilt on the stream (ordered before the kernel that reads
+// it). Returns nullptr when n is too large for a table or memory is short
+// (the search then computes its terms).
+const float2* pow_table(tsallis_ctx* c, long long n, float q, cudaStream_t stream) {
+    if (n < 1 || n > kPowTableMax) return nullptr;
+    if (c->ptab && c->ptab_n == n && c->ptab_q == q) return c->ptab;
+    if (!c->ptab || c->ptab_cap < n + 1) {
+        long long cap = c->ptab_cap > 0 ? c->ptab_cap : 65536;
+        while (cap < n + 1) cap *= 2;
+        if (c->ptab) {
+            if (cudaDeviceSynchronize() != cudaSuccess) return nullptr;
+            cudaFree(c->ptab);
+            c->ptab = nullptr;
+            c->ptab_cap = 0;
+        }
+        if (cudaMalloc(&c->ptab, (size_t)cap * sizeof(float2)) != cudaSuccess) {
+            cudaGetLastError();
+            c->ptab_n = -1;
+            return nullptr;
+        }
+        c->ptab_cap = cap;
+    }
+    if (build_pow_table(c->ptab, n, q, c->df_tables, stream) != cudaSuccess) {
+        cudaGetLastError();
+        c->ptab_n = -1;
+        return nullptr;
+    }
+    c->ptab_n = n;
+    c->ptab_q = q;
+    return c->ptab;
 }
 
 struct ScratchView {
@@ -405,6 +443,7 @@ void tsallis_destroy(tsallis_ctx* c) {
         if (c->s2_buf) cudaFree(c->s2_buf);
         if (c->df_tables) cudaFree(c->df_tables);
         if (c->log2_table) cudaFree(c->log2_table);
+        if (c->ptab) cudaFree(c->ptab);
     }
     delete c;
 }
@@ -591,6 +630,10 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
     a.exc_n = v.exc_n;
     a.exc_cap = kExcCap;
     a.exc_w = gvox <= (1ll << 20) ? kExcWindow : 0;   // positions are kept in 20 bits
+    if (p->mode == TSALLIS_PER_SLICE) {
+        a.ptab = pow_table(c, gvox, p->q, stream);
+        a.ptab_n = gvox;
+    }
     a.bq = v.bq;
     a.ghist = v.ghist;
     a.t_out = d_t;
@@ -700,6 +743,12 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
     bool small = true;
     for (const BatchVolDesc& v : vd) small = small && v.gvox <= (1ll << 20);
     a.exc_w = small ? kExcWindow : 0;
+    if (p->mode == TSALLIS_PER_SLICE) {
+        // slices of the first volume's size get the term table (others
+        // compute their terms)
+        a.ptab_n = vd[0].gvox;
+        a.ptab = pow_table(c, a.ptab_n, p->q, stream);
+    }
     a.bq = sv.bq;
     a.ghist = sv.ghist;
     a.t_out = d_t;

@@ -147,6 +147,9 @@ struct SearchSmem {
     long long best_na;
     int canon_t;
     int flag;
+    // per-warp running tops of the table search
+    float top_vh[kSearchWarps], top_vl[kSearchWarps], top_band[kSearchWarps], top_u2[kSearchWarps];
+    int top_i[kSearchWarps];
 };
 
 struct SearchResult {

@@ -76,6 +76,8 @@ struct SegArgs {
     int* status;
     float* curve;           // optional [ngroups][L-1]
     const void* df_tables;  // double-float log2/exp2 tables (device)
+    const float2* ptab;     // optional: terms 2^64 (n / ptab_n)^q (q = 1: n log2 n) for n = 0..ptab_n;
+    long long ptab_n;       // groups of exactly ptab_n voxels are searched with it
 };
 
 // A volume of a batch as the descriptor-expansion kernel receives it: its
@@ -114,6 +116,9 @@ int segment1d_threads();
 int segment1d_smem_bytes(int L, int copies);
 cudaError_t segment1d_occupancy(int copies, int L, int* blocks_per_sm);
 cudaError_t segment1d_prepare();
+// Term table of the table search for groups of n_max voxels, on stream s.
+cudaError_t build_pow_table(float2* tab, long long n_max, float q, const void* tables, cudaStream_t s);
+constexpr long long kPowTableMax = 1ll << 22;   // largest group size given a term table
 constexpr int kExcCap = 8192;      // first-pass exceptions kept per group
 constexpr int kExcWindow = 8;      // levels on each side of the predicted threshold
 

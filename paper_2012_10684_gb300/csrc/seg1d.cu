@@ -533,9 +533,13 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                     if (s_last) {
                         // this block completed the group: search it and publish
                         __threadfence();
-                        SearchResult r = search1d_block<WorkSync>(
-                            gh, a.L, a.q, a.curve ? a.curve + (long long)w.group * (a.L - 1) : nullptr, ssm, sT,
-                            sIC, dft);
+                        SearchResult r =
+                            (a.ptab != nullptr && gn == a.ptab_n && a.curve == nullptr)
+                                ? search1d_table<WorkSync>(gh, a.L, a.q, a.ptab, ssm, sT,
+                                                           reinterpret_cast<float2*>(sIC), dft)
+                                : search1d_block<WorkSync>(
+                                      gh, a.L, a.q, a.curve ? a.curve + (long long)w.group * (a.L - 1) : nullptr,
+                                      ssm, sT, sIC, dft);
                         // the first pass binarised with a predicted threshold t^:
                         // its mask is exact when no voxel has a level between
                         // t^ and t (no voxel changes side)
@@ -690,6 +694,25 @@ __global__ void k_build_log2_table(float2* __restrict__ lt, int n, const DfTable
         const F2 v = i >= 1 ? df_log2_u32((unsigned)i, T) : F2{0.f, 0.f};
         lt[i] = make_float2(v.hi, v.lo);
     }
+}
+
+// Terms of the table search: tab[n] = 2^64 (n / n_max)^q (q = 1: n log2 n)
+// as float pairs, the same values the search computes otherwise.
+__global__ void k_build_pow_table(float2* __restrict__ tab, long long n_max, float q, const DfTables* __restrict__ T) {
+    const F2 LN = df_log2_count<false>((unsigned)n_max, T);
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n <= n_max;
+         n += (long long)gridDim.x * blockDim.x) {
+        F2 v{0.f, 0.f};
+        if (n > 0) v = q == 1.0f ? df_hlog2h<false>((unsigned)n, T) : df_pow_ratio<false>((unsigned)n, LN, q, T);
+        tab[n] = make_float2(v.hi, v.lo);
+    }
+}
+
+cudaError_t build_pow_table(float2* tab, long long n_max, float q, const void* tables, cudaStream_t s) {
+    const long long blocks = (n_max + 256) / 256;
+    k_build_pow_table<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(tab, n_max, q,
+                                                                          static_cast<const DfTables*>(tables));
+    return cudaGetLastError();
 }
 
 cudaError_t build_log2_table(void* lt, int n, const void* tables, cudaStream_t s) {

@@ -221,3 +221,28 @@ def test_cluster_chunk_wait_timeout_reports_status_and_recovers():
         tg.set_wait_timeout(1_000_000_000)
     with kernel("cluster"):
         _check_step(v, "slice", 0.8)
+
+
+@pytest.mark.parametrize("kind", ["cluster", "tiles"])
+@pytest.mark.parametrize("q", [0.7, 1.0, 2.0])
+def test_exact_ties_between_mirror_partitions_are_reranked(kind, q):
+    """Three equal, disjoint blocks of levels: splitting after the first or
+    after the second gives mirror-image partitions with equal objective
+    values, so the maximum is a tie that the FP64 re-rank decides. The oracle
+    reports a zero gap; the threshold must be one of the two."""
+    v = np.empty((4, 48, 64), np.int16)   # 3072 voxels: three blocks of 1024
+    flat = v.reshape(4, -1)
+    for z in range(4):
+        flat[z] = np.repeat(np.array([-1000 + z, -500 + z, z], np.int16), 1024)
+    t_o, phi_o, gap_o, _ = oracle.segment1d(v, 48 * 64, f32(q), want_mask=False)
+    assert np.all(gap_o == 0)
+    with kernel(kind):
+        mask, t, phi, st = tg.tsallis_segment(_cuda(v), tg.tsallis_params(q=q))
+    torch.cuda.synchronize()
+    t, st = t.cpu().numpy(), st.cpu().numpy()
+    for z in range(4):
+        lv = np.unique(np.clip(flat[z].astype(np.int32) + 1024, 0, 4095))
+        assert t[z] in (lv[0], lv[1]), (z, t[z], lv)
+        assert abs(phi.cpu().numpy()[z] - phi_o[z]) <= 1e-5 * max(abs(phi_o[z]), 1.0)
+        assert (st[z] & 0xff) == 0
+        assert np.array_equal(mask[z].cpu().numpy().reshape(-1), oracle.binarize(flat[z], int(t[z])))
