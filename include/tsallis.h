@@ -56,6 +56,10 @@ typedef enum {
 
 /* Extra bits OR-ed into d_status entries (low byte holds a tsallis_status). */
 #define TSALLIS_STATUS_RERANKED 0x100  /* FP64 re-rank decided between near-tied candidates */
+#define TSALLIS_STATUS_WINDOW_HIT 0x400    /* window search: the maximiser was among the
+                                            proposed candidates */
+#define TSALLIS_STATUS_FALLBACK_SHIFT 16   /* window search: bits 16..23 hold how many
+                                              64-level blocks were searched exhaustively */
 #define TSALLIS_STATUS_FIRST_PASS_EXACT 0x200  /* the mask written in the histogram pass with a
                                                   predicted threshold was already exact, so the
                                                   group was not read a second time */
@@ -85,7 +89,9 @@ typedef struct {
     int32_t two_d;    /* 0: 1-D form; 1: 2-D grey x mean form. Default 0 */
     int32_t shift;    /* 2-D only: grey level = b >> shift, giving L2 = nbins >> shift
                          levels (2..256); default 4 */
-    int32_t topk;     /* 0: exhaustive search (default) */
+    int32_t topk;     /* 0: exhaustive search (default); 1..256: window search of the
+                         proposer's topk candidates, certified by per-block bounds
+                         (needs a proposer, see tsallis_proposer_set; 1-D, nbins 4096) */
     uint32_t flags;   /* TSALLIS_FLAG_* */
 } tsallis_params;
 
@@ -232,6 +238,50 @@ typedef struct {
 tsallis_status tsallis_segment_batch(tsallis_ctx* ctx, const tsallis_volume* h_vols, int32_t nvol,
                                      const tsallis_params* p, int32_t* d_t, float* d_phi, int32_t* d_status,
                                      cudaStream_t stream);
+
+/*
+ * Learned threshold proposer (an addition: the paper's search is exhaustive).
+ * A network reads x_k = log1p(counts of levels 16k..16k+15) / log1p(N),
+ * k < 256, of a 4096-level histogram and gives 4096 logits, one per
+ * threshold: z1 = W1 x + b1, a1 = GELU(z1), z2 = W2 a1 + b2, a2 = GELU(z2),
+ * z3 = W3 a2 + b3, with W1, W2 256 x 256 and W3 4096 x 256. Its parameters
+ * are one flat float vector of TSALLIS_PROPOSER_PARAMS values in the order
+ * W1, b1, W2, b2, W3, b3 (matrices row-major [out][in]); the GPU multiplies
+ * with bfloat16 copies of the matrices and accumulates in FP32. With
+ * params.topk = k > 0, tsallis_search, tsallis_segment and
+ * tsallis_segment_batch evaluate the objective first at the canonical
+ * thresholds of the k highest logits, then exhaustively in every block of
+ * 64 levels whose bound (from the class sums at its ends) could still reach
+ * that maximum: the result is that of the exhaustive search; the statuses
+ * report whether the window held the maximiser (TSALLIS_STATUS_WINDOW_HIT)
+ * and how many blocks were searched (bits TSALLIS_STATUS_FALLBACK_SHIFT..+7).
+ *
+ * tsallis_proposer_set / _get: copy the parameter vector to / from the
+ *   context (host memory, n must equal TSALLIS_PROPOSER_PARAMS; synchronous).
+ *   Setting also clears the optimiser state.
+ * tsallis_proposer_load / _save: the same through a file (8-byte magic
+ *   "TSPROP01", int64 count, the floats).
+ * tsallis_proposer_features: x [nh][256] (device) from histograms [nh][4096].
+ * tsallis_proposer_forward: logits [B][4096] (device) from x [B][256].
+ * tsallis_proposer_train_step: forward pass, mean cross-entropy of
+ *   softmax(logits) against target distributions y [B][4096] into *d_loss,
+ *   backward pass, and (update != 0) one Adam step (beta 0.9, 0.999,
+ *   eps 1e-8) with learning rate lr; d_grad (nullable) receives the
+ *   gradient [TSALLIS_PROPOSER_PARAMS]. Steps on one context are ordered on
+ *   the stream.
+ */
+#define TSALLIS_PROPOSER_PARAMS 1184256
+tsallis_status tsallis_proposer_set(tsallis_ctx* ctx, const float* h_params, int64_t n);
+tsallis_status tsallis_proposer_get(tsallis_ctx* ctx, float* h_params, int64_t n);
+tsallis_status tsallis_proposer_load(tsallis_ctx* ctx, const char* path);
+tsallis_status tsallis_proposer_save(tsallis_ctx* ctx, const char* path);
+tsallis_status tsallis_proposer_features(tsallis_ctx* ctx, const int32_t* d_hist, int64_t nh, float* d_x,
+                                         cudaStream_t stream);
+tsallis_status tsallis_proposer_forward(tsallis_ctx* ctx, const float* d_x, int32_t B, float* d_logits,
+                                        cudaStream_t stream);
+tsallis_status tsallis_proposer_train_step(tsallis_ctx* ctx, const float* d_x, const float* d_y, int32_t B,
+                                           float lr, int32_t update, float* d_loss, float* d_grad,
+                                           cudaStream_t stream);
 
 /*
  * Autotuner for tsallis_segment_batch (the counterpart of the paper's

@@ -11,7 +11,7 @@ histogram and proposes thresholds, so that the exact search can be confined
 to a window of candidates. Its definition, written out here once:
 
   features  x_k = log1p(sum_{j=16k}^{16k+15} h_j) / log1p(N), k = 0..255,
-            for a 4096-level histogram h with N counts;
+            for a 4096-level histogram h with N counts (all zero if N = 0);
   network   z1 = W1 x + b1, a1 = GELU(z1), z2 = W2 a1 + b2, a2 = GELU(z2),
             z3 = W3 a2 + b3 (4096 logits, one per threshold level), with
             W1, W2: 256 x 256, W3: 4096 x 256, GELU(z) = z Phi(z) =
@@ -59,7 +59,8 @@ def features(h):
     h = np.asarray(h, np.float64).reshape(-1, NOUT)
     s = h.reshape(h.shape[0], NIN, GROUP).sum(axis=2)
     n = h.sum(axis=1, keepdims=True)
-    return np.log1p(s) / np.log1p(n)
+    den = np.log1p(n)
+    return np.divide(np.log1p(s), den, out=np.zeros_like(s), where=den > 0)   # empty histogram: all zero
 
 
 def gelu(z):

@@ -88,6 +88,14 @@ _SIGS = {
     "tsallis_autotune_batch": ([_P, ctypes.POINTER(Volume), ctypes.c_int32, ctypes.POINTER(Params), _P, _P, _P, _P,
                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                 ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
+    "tsallis_proposer_set": ([_P, _P, _I64], ctypes.c_int),
+    "tsallis_proposer_get": ([_P, _P, _I64], ctypes.c_int),
+    "tsallis_proposer_load": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "tsallis_proposer_save": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "tsallis_proposer_features": ([_P, _P, _I64, _P, _P], ctypes.c_int),
+    "tsallis_proposer_forward": ([_P, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
+    "tsallis_proposer_train_step": ([_P, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32, _P, _P, _P],
+                                    ctypes.c_int),
     "tsallis_probe_dfmath": ([_P, _P, _I64, ctypes.c_uint32, ctypes.c_float, _P, _P, _P], ctypes.c_int),
 }
 
@@ -333,3 +341,67 @@ def tsallis_autotune_batch(vols, p: Params | None = None, masks=None, outs=None)
         context(vols[0].device), arr, len(vols), ctypes.byref(p), t.data_ptr(), phi.data_ptr(), st.data_ptr(),
         _stream(vols[0]), ctypes.byref(tv), ctypes.byref(bps), ctypes.byref(ms)))
     return tv.value, bps.value, ms.value
+
+
+# ---------------------------------------------------------------- proposer
+
+PROPOSER_PARAMS = 1184256
+TSALLIS_STATUS_WINDOW_HIT = 0x400
+TSALLIS_STATUS_FALLBACK_SHIFT = 16
+
+
+def proposer_set(params, device=None) -> None:
+    """Parameters of the learned proposer (flat float vector W1, b1, W2, b2,
+    W3, b3); clears the optimiser state."""
+    import numpy as np
+    a = np.ascontiguousarray(params, np.float32).reshape(-1)
+    if a.size != PROPOSER_PARAMS:
+        raise ValueError("expected %d parameters" % PROPOSER_PARAMS)
+    _check("tsallis_proposer_set", lib().tsallis_proposer_set(context(device), a.ctypes.data, a.size))
+
+
+def proposer_get(device=None):
+    import numpy as np
+    a = np.empty(PROPOSER_PARAMS, np.float32)
+    _check("tsallis_proposer_get", lib().tsallis_proposer_get(context(device), a.ctypes.data, a.size))
+    return a
+
+
+def proposer_load(path: str, device=None) -> None:
+    _check("tsallis_proposer_load", lib().tsallis_proposer_load(context(device), os.fsencode(path)))
+
+
+def proposer_save(path: str, device=None) -> None:
+    _check("tsallis_proposer_save", lib().tsallis_proposer_save(context(device), os.fsencode(path)))
+
+
+def proposer_features(hist: torch.Tensor) -> torch.Tensor:
+    """x [nh][256] from int32 histograms [nh][4096]."""
+    if not hist.is_cuda or hist.dtype != torch.int32 or not hist.is_contiguous() or hist.numel() % 4096:
+        raise TypeError("hist must be a contiguous int32 CUDA tensor of 4096-level histograms")
+    nh = hist.numel() // 4096
+    x = torch.empty((nh, 256), dtype=torch.float32, device=hist.device)
+    _check("tsallis_proposer_features", lib().tsallis_proposer_features(context(hist.device), hist.data_ptr(), nh,
+                                                                        x.data_ptr(), _stream(hist)))
+    return x
+
+
+def proposer_forward(x: torch.Tensor) -> torch.Tensor:
+    """Logits [B][4096] from features x [B][256] (float32, CUDA)."""
+    x = x.contiguous()
+    z = torch.empty((x.shape[0], 4096), dtype=torch.float32, device=x.device)
+    _check("tsallis_proposer_forward", lib().tsallis_proposer_forward(context(x.device), x.data_ptr(), x.shape[0],
+                                                                      z.data_ptr(), _stream(x)))
+    return z
+
+
+def proposer_train_step(x: torch.Tensor, y: torch.Tensor, lr: float = 1e-3, update: bool = True,
+                        want_grad: bool = False):
+    """One training step on a batch: returns (loss tensor [1], gradient or None)."""
+    x, y = x.contiguous(), y.contiguous()
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    g = torch.empty(PROPOSER_PARAMS, dtype=torch.float32, device=x.device) if want_grad else None
+    _check("tsallis_proposer_train_step", lib().tsallis_proposer_train_step(
+        context(x.device), x.data_ptr(), y.data_ptr(), x.shape[0], float(lr), 1 if update else 0, loss.data_ptr(),
+        g.data_ptr() if g is not None else None, _stream(x)))
+    return loss, g

@@ -2,6 +2,7 @@
 // checks, the context's scratch memory, and dispatch to the kernels.
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -11,6 +12,8 @@
 #include "kernels.h"
 
 using namespace tsl;
+
+static_assert(kMlpParams == TSALLIS_PROPOSER_PARAMS, "parameter count of the C ABI");
 
 struct tsallis_ctx {
     int device = 0;
@@ -44,6 +47,16 @@ struct tsallis_ctx {
     long long ptab_cap = 0;     // entries allocated
     long long ptab_n = -1;      // slice size it holds
     float ptab_q = 0.f;
+    // learned proposer: parameters (FP32, bfloat16, gradient, Adam moments),
+    // activations for up to mlp.cap rows, features and candidates
+    MlpBuffers mlp{};
+    void* mlp_params = nullptr;
+    void* mlp_act = nullptr;
+    int mlp_step = 0;               // Adam steps taken
+    bool mlp_ready = false;         // parameters were set
+    float* prop_x = nullptr;        // [prop_cap][256]
+    int32_t* prop_cand = nullptr;   // [prop_cap][256]
+    int prop_cap = 0;
 };
 
 namespace {
@@ -171,6 +184,96 @@ const float2* pow_table(tsallis_ctx* c, long long n, float q, cudaStream_t strea
     c->ptab_n = n;
     c->ptab_q = q;
     return c->ptab;
+}
+
+// Parameter block of the proposer: FP32 copy, gradient, two Adam moments
+// (kMlpParams floats each), then the bfloat16 copy.
+tsallis_status ensure_mlp_params(tsallis_ctx* c) {
+    if (c->mlp_params) return TSALLIS_OK;
+    const size_t f = (size_t)kMlpParams * sizeof(float);
+    const size_t bytes = 4 * f + (size_t)kMlpParams * 2;
+    if (cudaMalloc(&c->mlp_params, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->mlp_params = nullptr;
+        return TSALLIS_ERR_OOM;
+    }
+    char* b = static_cast<char*>(c->mlp_params);
+    c->mlp.p32 = reinterpret_cast<float*>(b);
+    c->mlp.grad = reinterpret_cast<float*>(b + f);
+    c->mlp.m = reinterpret_cast<float*>(b + 2 * f);
+    c->mlp.v = reinterpret_cast<float*>(b + 3 * f);
+    c->mlp.p16 = b + 4 * f;
+    if (cudaMemset(c->mlp_params, 0, bytes) != cudaSuccess) return TSALLIS_ERR_CUDA;
+    return TSALLIS_OK;
+}
+
+// Activations for `rows` rows of the proposer (grown, never shrunk; the
+// device is synchronised before a smaller buffer is replaced).
+tsallis_status ensure_mlp_act(tsallis_ctx* c, int rows) {
+    if (c->mlp_act && c->mlp.cap >= rows) return TSALLIS_OK;
+    int cap = c->mlp.cap > 0 ? c->mlp.cap : 256;
+    while (cap < rows) cap *= 2;
+    if (c->mlp_act) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
+        cudaFree(c->mlp_act);
+        c->mlp_act = nullptr;
+        c->mlp.cap = 0;
+    }
+    const size_t h = (size_t)cap * kMlpHid, o = (size_t)cap * kMlpOut;
+    if (cudaMalloc(&c->mlp_act, (6 * h + 2 * o) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return TSALLIS_ERR_OOM;
+    }
+    float* f = static_cast<float*>(c->mlp_act);
+    c->mlp.z1 = f; c->mlp.a1 = f + h; c->mlp.z2 = f + 2 * h; c->mlp.a2 = f + 3 * h;
+    c->mlp.da = f + 4 * h; c->mlp.dz = f + 5 * h;
+    c->mlp.z3 = f + 6 * h; c->mlp.d3 = f + 6 * h + o;
+    c->mlp.cap = cap;
+    return TSALLIS_OK;
+}
+
+constexpr int kPropChunk = 1024;   // histograms per proposer pass
+
+tsallis_status ensure_prop(tsallis_ctx* c, int rows) {
+    if (c->prop_x && c->prop_cap >= rows) return TSALLIS_OK;
+    if (c->prop_x) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
+        cudaFree(c->prop_x);
+        c->prop_x = nullptr;
+        c->prop_cand = nullptr;
+        c->prop_cap = 0;
+    }
+    void* b = nullptr;
+    if (cudaMalloc(&b, (size_t)rows * (kMlpIn * sizeof(float) + 256 * sizeof(int32_t))) != cudaSuccess) {
+        cudaGetLastError();
+        return TSALLIS_ERR_OOM;
+    }
+    c->prop_x = static_cast<float*>(b);
+    c->prop_cand = reinterpret_cast<int32_t*>(c->prop_x + (size_t)rows * kMlpIn);
+    c->prop_cap = rows;
+    return TSALLIS_OK;
+}
+
+// Window search of nh 1-D histograms: features, proposer, the top k
+// levels, then the certified window search (search1d.cuh).
+tsallis_status search_window(tsallis_ctx* c, const int32_t* d_hist, long long nh, const tsallis_params* p,
+                             int32_t* d_t, float* d_phi, int32_t* d_status, cudaStream_t stream) {
+    if (!c->mlp_ready) return TSALLIS_ERR_INVALID_ARG;   // no proposer was set
+    if (p->nbins != kMlpOut || p->two_d || p->topk < 1 || p->topk > 256) return TSALLIS_ERR_INVALID_ARG;
+    tsallis_status st;
+    const int chunk = (int)(nh < kPropChunk ? nh : kPropChunk);
+    if ((st = ensure_mlp_act(c, chunk)) != TSALLIS_OK || (st = ensure_prop(c, chunk)) != TSALLIS_OK) return st;
+    for (long long h0 = 0; h0 < nh; h0 += chunk) {
+        const int n = (int)(nh - h0 < chunk ? nh - h0 : chunk);
+        const int32_t* hist = d_hist + h0 * kMlpOut;
+        if (mlp_features(hist, n, c->prop_x, stream) != cudaSuccess ||
+            mlp_forward(c->mlp, c->prop_x, n, stream) != cudaSuccess ||
+            mlp_topk(c->mlp.z3, n, p->topk, c->prop_cand, stream) != cudaSuccess ||
+            launch_search1d_window(hist, n, kMlpOut, p->q, c->prop_cand, p->topk, d_t + h0, d_phi + h0,
+                                   d_status + h0, c->df_tables, stream) != cudaSuccess)
+            return TSALLIS_ERR_CUDA;
+    }
+    return TSALLIS_OK;
 }
 
 struct ScratchView {
@@ -444,6 +547,9 @@ void tsallis_destroy(tsallis_ctx* c) {
         if (c->df_tables) cudaFree(c->df_tables);
         if (c->log2_table) cudaFree(c->log2_table);
         if (c->ptab) cudaFree(c->ptab);
+        if (c->mlp_params) cudaFree(c->mlp_params);
+        if (c->mlp_act) cudaFree(c->mlp_act);
+        if (c->prop_x) cudaFree(c->prop_x);
     }
     delete c;
 }
@@ -528,6 +634,10 @@ tsallis_status tsallis_search(tsallis_ctx* c, const int32_t* d_hist, int64_t nh,
         return cuda_status(search2d_enqueue(c, c->s2_buf, d_hist, nh, p, d_t, nullptr, d_phi, d_status, d_curve,
                                             stream));
     }
+    if (p->topk > 0) {
+        if (d_curve) return TSALLIS_ERR_INVALID_ARG;   // the window search evaluates only some levels
+        return search_window(c, d_hist, nh, p, d_t, d_phi, d_status, stream);
+    }
     return cuda_status(launch_search1d(d_hist, nh, p->nbins, p->q, d_t, d_phi, d_status, d_curve, c->df_tables,
                                        stream));
 }
@@ -585,6 +695,10 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
     if (p->two_d) return segment2d(c, d_vol, nx, ny, nz, p, ng, gvox, d_mask, d_t, d_phi, d_status, stream);
+    if (p->topk > 0) {
+        const tsallis_volume v{d_vol, d_mask, nx, ny, nz};
+        return tsallis_segment_batch(c, &v, 1, p, d_t, d_phi, d_status, stream);
+    }
     if (use_slice_cluster(c, p, slice)) {
         if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
         ClusterArgs a;
@@ -724,6 +838,34 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
         ea.out = groups;
         if (launch_expand_groups(ea, stream) != cudaSuccess) return TSALLIS_ERR_CUDA;
     }
+    if (p->topk > 0) {
+        // window search: histograms, proposer + certified window search,
+        // then Algorithm 1 (three launches; volumes are read twice as in
+        // the one-launch path)
+        if (!c->mlp_ready || p->nbins != kMlpOut) return TSALLIS_ERR_INVALID_ARG;
+        ScratchView sv = view(c);
+        const size_t hb = (size_t)ng * kMaxLevels * sizeof(int);
+        SegArgs h;
+        fill_common(h, p, c);
+        h.groups = groups;
+        h.ngroups = (int)ng;
+        h.ntotal = (unsigned)ntot;
+        h.phases = kPhaseHist;
+        h.hdr = sv.hdr;
+        h.ghist = sv.ghist;
+        if (cudaMemsetAsync(sv.ghist, 0, hb, stream) != cudaSuccess ||
+            launch_segment1d(h, grid_for(c, h.ntotal), c->copies, stream) != cudaSuccess)
+            return TSALLIS_ERR_CUDA;
+        if ((st = search_window(c, sv.ghist, ng, p, d_t, d_phi, d_status, stream)) != TSALLIS_OK) return st;
+        SegArgs b = h;
+        b.phases = kPhaseBin;
+        b.t_in = d_t;
+        b.t_stride = 1;
+        if (cudaMemsetAsync(sv.ghist, 0, hb, stream) != cudaSuccess ||   // scratch left zeroed
+            launch_segment1d(b, grid_for(c, b.ntotal), c->copies, stream) != cudaSuccess)
+            return TSALLIS_ERR_CUDA;
+        return TSALLIS_OK;
+    }
     SegArgs a;
     fill_common(a, p, c);
     a.groups = groups;
@@ -755,6 +897,110 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
     a.phi_out = d_phi;
     a.status = d_status;
     return cuda_status(launch_segment1d(a, grid_for(c, a.ntotal), c->copies, stream));
+}
+
+tsallis_status tsallis_proposer_set(tsallis_ctx* c, const float* h_params, int64_t n) {
+    if (!c || !h_params || n != kMlpParams) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    tsallis_status st = ensure_mlp_params(c);
+    if (st != TSALLIS_OK) return st;
+    const size_t f = (size_t)kMlpParams * sizeof(float);
+    if (cudaMemcpy(c->mlp.p32, h_params, f, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->mlp.m, 0, f) != cudaSuccess || cudaMemset(c->mlp.v, 0, f) != cudaSuccess ||
+        mlp_to_bf16(c->mlp.p32, c->mlp.p16, kMlpParams, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return TSALLIS_ERR_CUDA;
+    c->mlp_step = 0;
+    c->mlp_ready = true;
+    return TSALLIS_OK;
+}
+
+tsallis_status tsallis_proposer_get(tsallis_ctx* c, float* h_params, int64_t n) {
+    if (!c || !h_params || n != kMlpParams || !c->mlp_ready) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(h_params, c->mlp.p32, (size_t)kMlpParams * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TSALLIS_ERR_CUDA;
+    return TSALLIS_OK;
+}
+
+namespace {
+const char kPropMagic[8] = {'T', 'S', 'P', 'R', 'O', 'P', '0', '1'};
+}
+
+tsallis_status tsallis_proposer_load(tsallis_ctx* c, const char* path) {
+    if (!c || !path) return TSALLIS_ERR_INVALID_ARG;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return TSALLIS_ERR_INVALID_ARG;
+    char magic[8];
+    int64_t n = 0;
+    std::vector<float> buf;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kPropMagic, 8) == 0 &&
+              std::fread(&n, sizeof(n), 1, f) == 1 && n == kMlpParams;
+    if (ok) {
+        buf.resize((size_t)n);
+        ok = std::fread(buf.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+    }
+    std::fclose(f);
+    if (!ok) return TSALLIS_ERR_INVALID_ARG;
+    return tsallis_proposer_set(c, buf.data(), n);
+}
+
+tsallis_status tsallis_proposer_save(tsallis_ctx* c, const char* path) {
+    if (!c || !path || !c->mlp_ready) return TSALLIS_ERR_INVALID_ARG;
+    std::vector<float> buf((size_t)kMlpParams);
+    tsallis_status st = tsallis_proposer_get(c, buf.data(), kMlpParams);
+    if (st != TSALLIS_OK) return st;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return TSALLIS_ERR_INVALID_ARG;
+    const int64_t n = kMlpParams;
+    const bool ok = std::fwrite(kPropMagic, 1, 8, f) == 8 && std::fwrite(&n, sizeof(n), 1, f) == 1 &&
+                    std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+    return (std::fclose(f) == 0 && ok) ? TSALLIS_OK : TSALLIS_ERR_INVALID_ARG;
+}
+
+tsallis_status tsallis_proposer_features(tsallis_ctx* c, const int32_t* d_hist, int64_t nh, float* d_x,
+                                         cudaStream_t stream) {
+    if (!c || nh < 0 || (nh > 0 && (!d_hist || !d_x))) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    return cuda_status(mlp_features(d_hist, nh, d_x, stream));
+}
+
+tsallis_status tsallis_proposer_forward(tsallis_ctx* c, const float* d_x, int32_t B, float* d_logits,
+                                        cudaStream_t stream) {
+    if (!c || B < 0 || (B > 0 && (!d_x || !d_logits)) || !c->mlp_ready) return TSALLIS_ERR_INVALID_ARG;
+    if (B == 0) return TSALLIS_OK;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    tsallis_status st = ensure_mlp_act(c, B);
+    if (st != TSALLIS_OK) return st;
+    if (mlp_forward(c->mlp, d_x, B, stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_logits, c->mlp.z3, (size_t)B * kMlpOut * sizeof(float), cudaMemcpyDeviceToDevice,
+                        stream) != cudaSuccess)
+        return TSALLIS_ERR_CUDA;
+    return TSALLIS_OK;
+}
+
+tsallis_status tsallis_proposer_train_step(tsallis_ctx* c, const float* d_x, const float* d_y, int32_t B, float lr,
+                                           int32_t update, float* d_loss, float* d_grad, cudaStream_t stream) {
+    if (!c || B < 1 || !d_x || !d_y || !d_loss || !c->mlp_ready || !(lr >= 0.f)) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    tsallis_status st = ensure_mlp_act(c, B);
+    if (st != TSALLIS_OK) return st;
+    if (mlp_forward(c->mlp, d_x, B, stream) != cudaSuccess ||
+        mlp_backward(c->mlp, d_x, d_y, B, d_loss, stream) != cudaSuccess)
+        return TSALLIS_ERR_CUDA;
+    if (d_grad && cudaMemcpyAsync(d_grad, c->mlp.grad, (size_t)kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  stream) != cudaSuccess)
+        return TSALLIS_ERR_CUDA;
+    if (update) {
+        c->mlp_step += 1;
+        if (mlp_adam(c->mlp, lr, c->mlp_step, stream) != cudaSuccess) return TSALLIS_ERR_CUDA;
+    }
+    return TSALLIS_OK;
 }
 
 tsallis_status tsallis_autotune_batch(tsallis_ctx* c, const tsallis_volume* h_vols, int32_t nvol,

@@ -148,6 +148,34 @@ cudaError_t slice_cluster_prepare();
 cudaError_t slice_cluster_occupancy(int* max_clusters);
 cudaError_t launch_slice_cluster(const ClusterArgs& a, int nclusters, cudaStream_t s);
 
+// Learned threshold proposer (mlp.cu): 256 features -> 256 -> 256 -> 4096.
+constexpr int kMlpIn = 256, kMlpHid = 256, kMlpOut = 4096, kMlpGroup = 16;
+constexpr long long kOffW1 = 0, kOffB1 = kOffW1 + (long long)kMlpHid * kMlpIn;
+constexpr long long kOffW2 = kOffB1 + kMlpHid, kOffB2 = kOffW2 + (long long)kMlpHid * kMlpHid;
+constexpr long long kOffW3 = kOffB2 + kMlpHid, kOffB3 = kOffW3 + (long long)kMlpOut * kMlpHid;
+constexpr long long kMlpParams = kOffB3 + kMlpOut;   // 1,184,256
+struct MlpBuffers {
+    float* p32;      // [kMlpParams] optimiser copy (biases are read from here)
+    void* p16;       // [kMlpParams] bfloat16 copy (matrices are read from here)
+    float* grad;     // [kMlpParams]
+    float* m;        // Adam moments
+    float* v;
+    // activations for up to `cap` rows
+    float *z1, *a1, *z2, *a2;   // [cap][256]
+    float *z3, *d3;             // [cap][4096]
+    float *da, *dz;             // [cap][256]
+    int cap;
+};
+cudaError_t mlp_features(const int32_t* hist, long long nh, float* x, cudaStream_t s);
+cudaError_t mlp_to_bf16(const float* p, void* p16, long long n, cudaStream_t s);
+cudaError_t mlp_forward(const MlpBuffers& b, const float* x, int B, cudaStream_t s);   // logits in b.z3
+cudaError_t mlp_backward(const MlpBuffers& b, const float* x, const float* y, int B, float* loss, cudaStream_t s);
+cudaError_t mlp_adam(const MlpBuffers& b, float lr, int step, cudaStream_t s);
+cudaError_t mlp_topk(const float* z, int B, int k, int32_t* out, cudaStream_t s);
+// Window search (seg1d.cu): nh histograms, k candidate levels each.
+cudaError_t launch_search1d_window(const int32_t* hist, long long nh, int L, float q, const int32_t* cand, int k,
+                                   int32_t* t, float* phi, int32_t* status, const void* tables, cudaStream_t s);
+
 // 2-D form (seg2d.cu).
 struct Hist2dLaunch {
     const int16_t* vol;

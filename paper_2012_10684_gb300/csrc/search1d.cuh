@@ -540,4 +540,284 @@ __device__ SearchResult search1d_table(const int32_t* __restrict__ h, int L, flo
     return SearchResult{t_win, phi_win, TSALLIS_OK | TSALLIS_STATUS_RERANKED};
 }
 
+// ------------------------------------------------------------ window search
+//
+// The exact search started from a window of candidate levels (a proposer's
+// ranking). The terms, sums and per-level objective are those of the table
+// search above, with the terms computed rather than read from a table. The
+// objective is first evaluated at the canonical thresholds of the candidates
+// (a candidate at an empty level stands for the non-empty level below it,
+// which gives the same partition). Then, for every block of 64 levels, a
+// bound on the objective over the block follows from the class sums at its
+// two ends, because N_1 and Q_1 grow and N_2 and Q_2 shrink as t grows:
+//   q < 1:  a b' <= Q_1(hi) Q_2(lo) / ((N_1(lo) N_2(hi)) / N^2)^q,
+//           phi = (a b' - 1) / (1 - q) grows with a b';
+//   q > 1:  a b' >= Q_1(lo) Q_2(hi) / ((N_1(hi) N_2(lo)) / N^2)^q,
+//           phi = (1 - a b') / (q - 1) falls with a b';
+//   q = 1:  H_1 <= log N_1(hi) - S_1(lo) / N_1(hi) and
+//           H_2 <= log N_2(lo) - S_2(hi) / N_2(lo) (S = sum h log h >= 0).
+// Every block whose bound reaches the window's maximum (less its error
+// bound) is searched exhaustively, so the result is the exhaustive search's
+// result. A block with an empty class 1 at its start or an empty class 2 at
+// its end has no finite bound and is always searched.
+struct WindowSmem {
+    long long na_lo[64], na_hi[64];
+    float qa_lo[64][2], qa_hi[64][2], qb_lo[64][2], qb_hi[64][2];
+    unsigned char fallback[64];
+    unsigned char sel[kMaxBins];   // bit 0: proposed level; bit 1: evaluated in the window
+    int nfb;
+};
+
+__device__ __forceinline__ float window_block_bound(const WindowSmem& ws, int b, long long N, F2 LN, float q,
+                                                    const DfTables* __restrict__ T) {
+    const long long na_lo = ws.na_lo[b], na_hi = ws.na_hi[b];
+    const long long nb_lo = N - na_lo, nb_hi = N - na_hi;
+    if (na_hi <= 0 || nb_lo <= 0) return -INFINITY;   // no threshold of the block has two classes
+    const F2 qa_lo{ws.qa_lo[b][0], ws.qa_lo[b][1]}, qa_hi{ws.qa_hi[b][0], ws.qa_hi[b][1]};
+    const F2 qb_lo{ws.qb_lo[b][0], ws.qb_lo[b][1]}, qb_hi{ws.qb_hi[b][0], ws.qb_hi[b][1]};
+    F2 u;
+    if (q == 1.0f) {
+        const F2 la = df_log2_count<false>((unsigned)na_hi, T), lb = df_log2_count<false>((unsigned)nb_lo, T);
+        const F2 sa = df_div(qa_lo, df_from_u32((unsigned)na_hi)), sb = df_div(qb_hi, df_from_u32((unsigned)nb_lo));
+        u = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
+    } else if (q < 1.0f) {
+        if (na_lo <= 0 || nb_hi <= 0) return INFINITY;
+        const F2 pa = df_pow_ratio<false>((unsigned)na_lo, LN, q, T), pb = df_pow_ratio<false>((unsigned)nb_hi, LN, q, T);
+        const F2 ab = df_mul(df_div(qa_hi, pa), df_div(qb_lo, pb));
+        u = df_div(df_add(ab, F2{-1.0f, 0.f}), two_sum(1.0f, -q));
+    } else {
+        const F2 pa = df_pow_ratio<false>((unsigned)na_hi, LN, q, T), pb = df_pow_ratio<false>((unsigned)nb_lo, LN, q, T);
+        const F2 ab = df_mul(df_div(qa_lo, pa), df_div(qb_hi, pb));
+        u = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), two_sum(q, -1.0f));
+    }
+    const float v = u.hi + u.lo;
+    return v + 1e-9f * fabsf(v) + 1e-30f;   // the bound's own rounding
+}
+
+template <class Sync>
+__device__ SearchResult search1d_window(const int32_t* __restrict__ h, int L, float q, const int32_t* __restrict__ cand,
+                                        int ncand, SearchSmem& sm, WindowSmem& ws, float2* __restrict__ sW,
+                                        float2* __restrict__ sQ, const DfTables* __restrict__ T) {
+    const int tid = Sync::tid(), lane = tid & 31, warp = tid >> 5;
+    const bool shannon = (q == 1.0f);
+    const int base = tid * kBinsPerThread;
+
+    int hv[kBinsPerThread];
+    int c = 0, lastnz = -1;
+#pragma unroll
+    for (int k = 0; k < kBinsPerThread; ++k) {
+        hv[k] = base + k < L ? __ldcg(h + base + k) : 0;
+        c += hv[k];
+        if (hv[k] > 0) lastnz = base + k;
+        ws.sel[base + k] = 0;
+    }
+    // counts (prefix, total) and the last non-empty level before each thread
+    long long ci = c;
+    int li = lastnz;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const long long oc = __shfl_up_sync(0xffffffffu, ci, d);
+        const int ol = __shfl_up_sync(0xffffffffu, li, d);
+        if (lane >= d) { ci += oc; li = max(li, ol); }
+    }
+    if (lane == 31) { sm.cnt_pre[warp] = ci; sm.red_i[warp] = li; }
+    Sync::sync();
+    if (warp == 0) {
+        const long long cw = lane < kSearchWarps ? sm.cnt_pre[lane] : 0;
+        const int lw = lane < kSearchWarps ? sm.red_i[lane] : -1;
+        long long cc = cw;
+        int ll = lw;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long oc = __shfl_up_sync(0xffffffffu, cc, d);
+            const int ol = __shfl_up_sync(0xffffffffu, ll, d);
+            if (lane >= d) { cc += oc; ll = max(ll, ol); }
+        }
+        int le = __shfl_up_sync(0xffffffffu, ll, 1);
+        if (lane == 0) le = -1;
+        const long long tot = __shfl_sync(0xffffffffu, cc, kSearchWarps - 1);
+        __syncwarp();
+        if (lane < kSearchWarps) { sm.cnt_pre[lane] = cc - cw; sm.red_i[lane] = le; }
+        if (lane == 0) sm.total = tot;
+    }
+    // proposed levels
+    for (int i = tid; i < ncand; i += kSearchThreads) {
+        const int t = cand[i];
+        if (t >= 0 && t < L) ws.sel[t] = 1;
+    }
+    Sync::sync();
+    const long long N = sm.total;
+    long long c_before = __shfl_up_sync(0xffffffffu, ci, 1);
+    int l_before = __shfl_up_sync(0xffffffffu, li, 1);
+    if (lane == 0) { c_before = 0; l_before = -1; }
+    c_before += sm.cnt_pre[warp];
+    l_before = max(l_before, sm.red_i[warp]);
+    // a proposed level stands for the last non-empty level at or below it
+    {
+        int last = l_before;
+#pragma unroll
+        for (int k = 0; k < kBinsPerThread; ++k) {
+            if (hv[k] > 0) last = base + k;
+            if ((ws.sel[base + k] & 1) && last >= 0) ws.sel[last] |= 2;
+        }
+    }
+
+    // terms, running sums, block scans (as in the table search)
+    const F2 LN = shannon ? F2{0.f, 0.f} : df_log2_count<false>((unsigned)N, T);
+    F2 run{0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < kBinsPerThread; ++k) {
+        F2 w{0.f, 0.f};
+        if (hv[k] > 0) w = shannon ? df_hlog2h<false>((unsigned)hv[k], T) : df_pow_ratio<false>((unsigned)hv[k], LN, q, T);
+        sW[base + k] = make_float2(w.hi, w.lo);
+        run = f2_add(run, w);
+        sQ[base + k] = make_float2(run.hi, run.lo);
+    }
+    F2 pi = run, si = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const F2 op = shfl_up_f2(pi, d);
+        const F2 os = shfl_down_f2(si, d);
+        if (lane >= d) pi = f2_add(op, pi);
+        if (lane + d < 32) si = f2_add(si, os);
+    }
+    if (lane == 31) sm.w_pre[warp] = pi;
+    if (lane == 0) sm.w_suf[warp] = si;
+    Sync::sync();
+    if (warp == 0) {
+        F2 pp = lane < kSearchWarps ? sm.w_pre[lane] : F2{0.f, 0.f};
+        F2 ss = lane < kSearchWarps ? sm.w_suf[lane] : F2{0.f, 0.f};
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const F2 op = shfl_up_f2(pp, d);
+            const F2 os = shfl_down_f2(ss, d);
+            if (lane >= d) pp = f2_add(op, pp);
+            if (lane + d < 32) ss = f2_add(ss, os);
+        }
+        F2 pe = shfl_up_f2(pp, 1);
+        if (lane == 0) pe = F2{0.f, 0.f};
+        const F2 se = shfl_down_f2(ss, 1);
+        __syncwarp();
+        if (lane < kSearchWarps) { sm.w_pre[lane] = pe; sm.w_suf[lane] = se; }
+    }
+    Sync::sync();
+    F2 w_before = shfl_up_f2(pi, 1);
+    F2 w_after = shfl_down_f2(si, 1);
+    if (lane == 0) w_before = F2{0.f, 0.f};
+    if (lane == 31) w_after = F2{0.f, 0.f};
+    w_before = f2_add(sm.w_pre[warp], w_before);
+    w_after = f2_add(w_after, sm.w_suf[warp]);
+
+    const F2 qm1 = two_sum(q, -1.0f);
+    // objective at level k of this thread (valid: non-empty, class 2 non-empty)
+    auto eval = [&](int k, long long na, F2 QA, F2 QB, F2& phi, float& band, double* f64) {
+        const long long nb = N - na;
+        if (shannon) {
+            const F2 la = df_log2_count<false>((unsigned)na, T), lb = df_log2_count<false>((unsigned)nb, T);
+            const F2 sa = df_div(QA, df_from_u32((unsigned)na)), sb = df_div(QB, df_from_u32((unsigned)nb));
+            phi = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
+            band = shannon_band_df(la.hi, sa.hi, lb.hi, sb.hi);
+            if (f64)
+                *f64 = 0.6931471805599453 * ((df_to_double(la) - df_to_double(QA) / (double)na) +
+                                             (df_to_double(lb) - df_to_double(QB) / (double)nb));
+        } else {
+            const F2 pa = df_pow_ratio<false>((unsigned)na, LN, q, T), pb = df_pow_ratio<false>((unsigned)nb, LN, q, T);
+            const F2 ab = df_mul(df_div(QA, pa), df_div(QB, pb));
+            phi = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), qm1);
+            band = tsallis_band_df(ab.hi, phi.hi, q);
+            if (f64)
+                *f64 = (1.0 - (df_to_double(QA) / df_to_double(pa)) * (df_to_double(QB) / df_to_double(pb))) /
+                       ((double)q - 1.0);
+        }
+    };
+    // pass over this thread's levels, right to left; mode 0: the window,
+    // and the class sums at the ends of each 64-level block; mode 1: the
+    // window and the fallback blocks; mode 2: FP64 at levels within lower
+    auto sweep = [&](int mode, float lower, Top& tp, double& bv, int& bi) {
+        long long na = c_before + c;
+        F2 rs{0.f, 0.f};
+        const bool fb = mode >= 1 && ws.fallback[tid >> 3];
+        for (int k = kBinsPerThread - 1; k >= 0; --k) {
+            const F2 QA = f2_add(w_before, F2{sQ[base + k].x, sQ[base + k].y});
+            const F2 QB = f2_add(rs, w_after);
+            if (mode == 0 && k == 0 && (tid & 7) == 0) {
+                ws.na_lo[tid >> 3] = na;
+                ws.qa_lo[tid >> 3][0] = QA.hi; ws.qa_lo[tid >> 3][1] = QA.lo;
+                ws.qb_lo[tid >> 3][0] = QB.hi; ws.qb_lo[tid >> 3][1] = QB.lo;
+            }
+            if (mode == 0 && k == kBinsPerThread - 1 && (tid & 7) == 7) {
+                ws.na_hi[tid >> 3] = na;
+                ws.qa_hi[tid >> 3][0] = QA.hi; ws.qa_hi[tid >> 3][1] = QA.lo;
+                ws.qb_hi[tid >> 3][0] = QB.hi; ws.qb_hi[tid >> 3][1] = QB.lo;
+            }
+            const bool valid = hv[k] > 0 && N - na > 0;
+            if (valid && ((ws.sel[base + k] & 2) || fb)) {
+                F2 phi;
+                float band;
+                double f = 0.0;
+                eval(k, na, QA, QB, phi, band, mode == 2 ? &f : nullptr);
+                if (mode < 2) tp = top_merge(Top{phi, base + k, band, -INFINITY}, tp);
+                else if (phi.hi + band >= lower) argmax_merge(bv, bi, f, base + k);
+            }
+            const float2 wk = sW[base + k];
+            rs = f2_add(F2{wk.x, wk.y}, rs);
+            na -= hv[k];
+        }
+    };
+    auto block_top = [&](Top tp) -> Top {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) tp = top_merge(tp, shfl_top(tp, d));
+        if (lane == 0) {
+            sm.top_vh[warp] = tp.v.hi;
+            sm.top_vl[warp] = tp.v.lo;
+            sm.top_i[warp] = tp.i;
+            sm.top_band[warp] = tp.band;
+            sm.top_u2[warp] = tp.u2;
+        }
+        Sync::sync();
+        Top g{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
+#pragma unroll
+        for (int w = 0; w < kSearchWarps; ++w)
+            g = top_merge(g, Top{{sm.top_vh[w], sm.top_vl[w]}, sm.top_i[w], sm.top_band[w], sm.top_u2[w]});
+        Sync::sync();
+        return g;
+    };
+    double bv = -INFINITY;
+    int bi = -1;
+    Top tp{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
+    sweep(0, 0.f, tp, bv, bi);
+    const Top gw = block_top(tp);    // the window's maximum (also publishes the block ends)
+    // blocks whose bound reaches the window's maximum
+    if (tid < 64) {
+        const float lower = gw.i >= 0 ? gw.v.hi - gw.band : -INFINITY;
+        const F2 LNb = shannon ? F2{0.f, 0.f} : LN;
+        ws.fallback[tid] = (64 * tid < L) && window_block_bound(ws, tid, N, LNb, q, T) >= lower;
+    }
+    if (tid == 0) ws.nfb = 0;
+    Sync::sync();
+    if (tid < 64 && ws.fallback[tid]) atomicAdd(&ws.nfb, 1);
+    tp = Top{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
+    sweep(1, 0.f, tp, bv, bi);
+    const Top g = block_top(tp);
+    const int nfb = ws.nfb;
+    if (g.i < 0) {
+        Sync::sync();
+        return SearchResult{-1, 0.f, TSALLIS_ERR_NO_VALID_THRESHOLD | (nfb << 16)};
+    }
+    int t_win = g.i;
+    float phi_win = g.v.hi + g.v.lo;
+    int status = TSALLIS_OK;
+    if (g.u2 >= g.v.hi - g.band) {
+        sweep(2, g.v.hi - g.band, tp, bv, bi);
+        block_argmax_d<Sync>(bv, bi, sm);
+        t_win = sm.red_i[0];
+        phi_win = (float)sm.red_dv[0];
+        status |= TSALLIS_STATUS_RERANKED;
+        Sync::sync();
+    }
+    if (ws.sel[t_win] & 2) status |= TSALLIS_STATUS_WINDOW_HIT;
+    Sync::sync();
+    return SearchResult{t_win, phi_win, status | (nfb << 16)};
+}
+
 }  // namespace tsl

@@ -676,6 +676,38 @@ __global__ void __launch_bounds__(kSearchThreads) k_search1d(const int32_t* __re
     }
 }
 
+// The window search, one block per histogram (search1d_window).
+__global__ void __launch_bounds__(kSearchThreads) k_search1d_window(const int32_t* __restrict__ hist, long long nh,
+                                                                    int L, float q, const int32_t* __restrict__ cand,
+                                                                    int k, int32_t* __restrict__ t_out,
+                                                                    float* __restrict__ phi_out,
+                                                                    int32_t* __restrict__ status,
+                                                                    const DfTables* __restrict__ dft) {
+    __shared__ SearchSmem sm;
+    __shared__ WindowSmem ws;
+    extern __shared__ int4 smem_window[];
+    float2* sW = reinterpret_cast<float2*>(smem_window);
+    float2* sQ = sW + kMaxBins;
+    for (long long g = blockIdx.x; g < nh; g += gridDim.x) {
+        SearchResult r = search1d_window<BlockSync>(hist + g * L, L, q, cand + g * k, k, sm, ws, sW, sQ, dft);
+        if (threadIdx.x == 0) {
+            t_out[g] = r.t;
+            phi_out[g] = r.phi;
+            status[g] = r.status;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_search1d_window(const int32_t* hist, long long nh, int L, float q, const int32_t* cand, int k,
+                                   int32_t* t, float* phi, int32_t* status, const void* tables, cudaStream_t s) {
+    if (nh <= 0) return cudaSuccess;
+    const int grid = (int)(nh < 65535 ? nh : 65535);
+    k_search1d_window<<<grid, kSearchThreads, 2 * kMaxBins * (int)sizeof(float2), s>>>(
+        hist, nh, L, q, cand, k, t, phi, status, static_cast<const DfTables*>(tables));
+    return cudaGetLastError();
+}
+
 // Test hook: the double-float power and log2 used by the search, for
 // checking their accuracy against an independent double-precision result.
 __global__ void k_probe_dfmath(const unsigned* __restrict__ h, long long n, unsigned N, float q,
@@ -791,6 +823,8 @@ cudaError_t segment1d_prepare() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_segment1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   segment1d_smem_bytes(kMaxBins, 1))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_search1d_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  2 * kMaxBins * (int)sizeof(float2))) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_search1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kMaxBins * (int)(sizeof(float2) + sizeof(int2)));
 }

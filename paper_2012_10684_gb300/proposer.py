@@ -1,0 +1,118 @@
+"""Training of the learned threshold proposer, on the GPU, through the C ABI.
+
+Data: seeded chest phantoms (512 x 512 x D, D uniform in [dmin, dmax], sensor
+noise sd uniform in [5, 30] HU, 4-8 airway generations), generated on the
+GPU one at a time. For each volume the 4096-level whole-volume histogram is
+computed (tsallis_histogram) and labelled with the exhaustive search's
+threshold (tsallis_search); the volume itself is not kept. The target of a
+histogram is the uniform distribution over the thresholds that give the
+labelled partition (the labelled level and the empty levels after it).
+
+Training: Adam on the mean soft-target cross-entropy (the library's
+forward, backward and optimiser kernels), minibatches drawn with a seeded
+generator. The result is written with tsallis_proposer_save.
+
+    python -m paper_2012_10684_gb300.proposer --out weights.bin
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import time
+
+import numpy as np
+import torch
+
+import paper_2012_10684_gb300 as tg
+
+
+def soft_targets(hist: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
+    """y [n][4096]: uniform over [t, e) where e is the first non-empty level
+    after t (rows with t = -1 stay zero)."""
+    n = hist.shape[0]
+    idx = torch.arange(4096, device=hist.device).expand(n, 4096)
+    tt = t.to(torch.int64).view(-1, 1)
+    after = (hist > 0) & (idx > tt)
+    e = torch.where(after, idx, torch.full_like(idx, 4095)).min(dim=1, keepdim=True).values
+    y = ((idx >= tt) & (idx < e) & (tt >= 0)).to(torch.float32)
+    s = y.sum(dim=1, keepdim=True)
+    return y / torch.where(s > 0, s, torch.ones_like(s))
+
+
+def make_dataset(n: int, seed: int, dmin: int, dmax: int, q: float = 0.8, nx: int = 512, ny: int = 512,
+                 device="cuda", log_every: int = 0):
+    """(hist [n][4096] int32, t [n] int32) from n generated volumes."""
+    import phantom
+    rng = np.random.default_rng(seed)
+    p = tg.tsallis_params(q=q, mode="volume")
+    hist = torch.empty((n, 4096), dtype=torch.int32, device=device)
+    buf = torch.empty(dmax * ny * nx, dtype=torch.int16, device=device)
+    t0 = time.time()
+    for i in range(n):
+        nz = int(rng.integers(dmin, dmax + 1))
+        spec = phantom.chest_volume(seed * 100000 + i, nx, ny, nz, generations=int(rng.integers(4, 9)),
+                                    noise_sd=int(rng.integers(5, 31)), vol_id=i)
+        vol = buf[: nz * ny * nx].view(nz, ny, nx)
+        phantom.generate_cuda(spec, out=vol)
+        tg.tsallis_histogram(vol, p, hist[i:i + 1])
+        if log_every and (i + 1) % log_every == 0:
+            print("generated %d volumes, %.1f s" % (i + 1, time.time() - t0), flush=True)
+    t, _, st = tg.tsallis_search(hist, p)
+    return hist, t, st
+
+
+def train(x: torch.Tensor, y: torch.Tensor, steps: int, batch: int, lr: float, seed: int, init_seed: int = 1,
+          log_every: int = 0):
+    """Trains the context's proposer from a seeded initialisation; returns
+    the loss of every step."""
+    g = np.random.default_rng(init_seed)
+    params = []
+    for fan_out, fan_in in ((256, 256), (256, 256), (4096, 256)):
+        bound = math.sqrt(6.0 / (fan_in + fan_out))
+        params.append(g.uniform(-bound, bound, fan_out * fan_in))
+        params.append(np.zeros(fan_out))
+    tg.proposer_set(np.concatenate(params).astype(np.float32), x.device)
+    gen = torch.Generator(device=x.device)
+    gen.manual_seed(seed)
+    losses = torch.empty(steps, dtype=torch.float32, device=x.device)
+    n = x.shape[0]
+    for s in range(steps):
+        # cosine decay of the learning rate
+        lr_s = lr * 0.5 * (1 + math.cos(math.pi * s / steps))
+        idx = torch.randint(0, n, (batch,), device=x.device, generator=gen)
+        loss, _ = tg.proposer_train_step(x[idx], y[idx], lr_s)
+        losses[s] = loss[0]
+        if log_every and (s + 1) % log_every == 0:
+            print("step %d loss %.4f" % (s + 1, float(losses[s])), flush=True)
+    return losses.cpu().numpy()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--volumes", type=int, default=20000)
+    ap.add_argument("--dmin", type=int, default=120)
+    ap.add_argument("--dmax", type=int, default=600)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=2012106845)
+    ap.add_argument("--out", required=True)
+    args = ap.parse_args()
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    hist, t, st = make_dataset(args.volumes, args.seed, args.dmin, args.dmax, log_every=1000)
+    assert bool(((st & 0xff) == 0).all())
+    x = tg.proposer_features(hist)
+    y = soft_targets(hist, t)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    losses = train(x, y, args.steps, args.batch, args.lr, args.seed, log_every=500)
+    torch.cuda.synchronize()
+    tg.proposer_save(args.out)
+    print("data %.1f s, training %.1f s, final loss %.4f" % (t1 - t0, time.time() - t1, losses[-100:].mean()))
+
+
+if __name__ == "__main__":
+    main()

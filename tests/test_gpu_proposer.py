@@ -1,0 +1,209 @@
+"""GPU tests of the learned threshold proposer and of the window search.
+
+Against the FP64 oracle (oracle/mlp.py, with the same bfloat16-rounded
+matrices the GPU multiplies with): features, logits, gradients, one Adam
+step. The window search (params.topk > 0) must give the exhaustive search's
+threshold on every histogram, whatever the proposer says (random weights
+included): 0 misses after fallback. With the trained weights, a test shows
+what the proposer gains: how often its window already holds the maximiser
+and how many 64-level blocks still need an exhaustive search, against the
+same search with an uninformed proposer."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import phantom
+import paper_2012_10684_gb300 as tg
+from oracle import mlp
+from paper_2012_10684_gb300 import proposer as P
+from test_gpu_1d import check_thresholds, f32
+
+pytestmark = pytest.mark.gpu
+
+WEIGHTS = os.path.join(os.path.dirname(tg.__file__), "proposer_weights.bin")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+
+
+def _params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, s in mlp.SHAPES:
+        fan_in = s[-1] if len(s) == 2 else 256
+        out.append(rng.normal(0, scale / np.sqrt(fan_in), int(np.prod(s))))
+    return np.concatenate(out).astype(np.float32)
+
+
+def _as_used(params):
+    """The parameters as the GPU uses them: matrices rounded to bfloat16,
+    biases as stored (float32), in FP64."""
+    d = mlp.unpack(np.asarray(params, np.float64))
+    return mlp.pack({k: (mlp.bf16_round(v) if k.startswith("W") else v) for k, v in d.items()})
+
+
+def _histograms(seed, n):
+    rng = np.random.default_rng(seed)
+    h = np.zeros((n, 4096), np.int32)
+    for i in range(n):
+        k = rng.integers(2, 600)
+        lv = rng.choice(4096, k, replace=False)
+        h[i, lv] = rng.integers(1, 5000, k)
+    return h
+
+
+def test_features_match_oracle():
+    v = phantom.generate_host(phantom.chest_volume(41, nz=20))
+    hp = tg.tsallis_histogram(torch.from_numpy(v).cuda(), tg.tsallis_params(mode="slice"))
+    h = torch.cat([hp, torch.from_numpy(_histograms(1, 30)).cuda(), torch.zeros((1, 4096), dtype=torch.int32,
+                                                                                device="cuda")])
+    x = tg.proposer_features(h).cpu().numpy()
+    xo = mlp.features(h.cpu().numpy())
+    assert np.allclose(x, xo, rtol=2e-6, atol=2e-7)
+
+
+def test_forward_matches_oracle():
+    params = _params(2)
+    tg.proposer_set(params)
+    x = np.random.default_rng(3).random((37, 256)).astype(np.float32)
+    z = tg.proposer_forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    zo, _ = mlp.forward(_as_used(params), x)
+    assert np.max(np.abs(z - zo)) <= 1e-4 * (1 + np.max(np.abs(zo)))
+
+
+def test_gradients_match_oracle():
+    params = _params(4)
+    tg.proposer_set(params)
+    rng = np.random.default_rng(5)
+    B = 6
+    x = rng.random((B, 256)).astype(np.float32)
+    h = _histograms(6, B)
+    t = np.array([int(np.flatnonzero(h[i])[len(np.flatnonzero(h[i])) // 2]) for i in range(B)])
+    y = mlp.targets(h, t).astype(np.float32)
+    loss, g = tg.proposer_train_step(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), update=False,
+                                     want_grad=True)
+    lo, go = mlp.grads(_as_used(params), x, y)
+    assert float(loss[0]) == pytest.approx(lo, rel=1e-5)
+    g = g.cpu().numpy()
+    o = 0
+    for name, s in mlp.SHAPES:
+        n = int(np.prod(s))
+        a, b = g[o:o + n], go[o:o + n]
+        assert np.max(np.abs(a - b)) <= 2e-3 * np.max(np.abs(b)) + 1e-8, name
+        o += n
+
+
+def test_adam_step_matches_oracle():
+    params = _params(7)
+    tg.proposer_set(params)
+    rng = np.random.default_rng(8)
+    x = torch.from_numpy(rng.random((4, 256)).astype(np.float32)).cuda()
+    y = torch.zeros((4, 4096), device="cuda")
+    y[:, 1000] = 1
+    _, g = tg.proposer_train_step(x, y, lr=1e-3, update=True, want_grad=True)
+    p1 = tg.proposer_get()
+    po, _, _ = mlp.adam_step(params.astype(np.float64), g.cpu().numpy().astype(np.float64),
+                             np.zeros(mlp.NPARAM), np.zeros(mlp.NPARAM), 1, 1e-3)
+    assert np.allclose(p1, po, rtol=1e-5, atol=1e-7)
+
+
+def test_save_load_round_trip(tmp_path):
+    params = _params(9)
+    tg.proposer_set(params)
+    f = str(tmp_path / "w.bin")
+    tg.proposer_save(f)
+    tg.proposer_set(np.zeros_like(params))
+    tg.proposer_load(f)
+    assert np.array_equal(tg.proposer_get(), params)
+
+
+def test_training_reduces_the_loss():
+    v = torch.from_numpy(phantom.generate_host(phantom.chest_volume(43, nz=64))).cuda()
+    p = tg.tsallis_params(q=0.8, mode="slice")
+    h = tg.tsallis_histogram(v, p)
+    t, _, _ = tg.tsallis_search(h, p)
+    x, y = tg.proposer_features(h), P.soft_targets(h, t)
+    losses = P.train(x, y, steps=300, batch=32, lr=2e-3, seed=1)
+    assert losses[-20:].mean() < 0.5 * losses[:5].mean(), (losses[:5], losses[-20:])
+
+
+def _window_vs_exhaustive(h, q, k=64):
+    p0 = tg.tsallis_params(q=q)
+    pk = tg.tsallis_params(q=q, topk=k)
+    t0, phi0, st0 = tg.tsallis_search(h, p0)
+    tk, phik, stk = tg.tsallis_search(h, pk)
+    return (t0.cpu().numpy(), phi0.cpu().numpy(), st0.cpu().numpy(), tk.cpu().numpy(), phik.cpu().numpy(),
+            stk.cpu().numpy())
+
+
+@pytest.mark.parametrize("q", [0.5, 0.8, 1.0, 1.5, 3.0])
+@pytest.mark.parametrize("weights", ["random", "zero"])
+def test_window_search_gives_the_exhaustive_result(q, weights):
+    tg.proposer_set(_params(10) if weights == "random" else np.zeros(mlp.NPARAM, np.float32))
+    v = phantom.generate_host(phantom.chest_volume(45, nz=48))
+    hv = tg.tsallis_histogram(torch.from_numpy(v).cuda(), tg.tsallis_params(mode="slice"))
+    h = torch.cat([hv, torch.from_numpy(_histograms(11, 40)).cuda()])
+    special = np.zeros((4, 4096), np.int32)
+    special[0, 7] = 10                          # one level: no threshold
+    special[1, [0, 4095]] = [3, 4]              # two levels far apart
+    special[2, 100:164] = 5                     # one full block
+    special[3, ::2] = 1                         # every other level
+    h = torch.cat([h, torch.from_numpy(special).cuda()])
+    t0, phi0, st0, tk, phik, stk = _window_vs_exhaustive(h, q)
+    hh = h.cpu().numpy()
+    t_o, phi_o, gap_o = [], [], []
+    for i in range(hh.shape[0]):
+        a, b, c, _, _ = oracle.search1d(hh[i], f32(q))
+        t_o.append(a); phi_o.append(b); gap_o.append(c)
+    check_thresholds(tk, phik, stk & 0xff, t_o, phi_o, gap_o, ("window", q, weights))
+    same = np.array(gap_o) >= 1e-9
+    assert np.array_equal(tk[same], t0[same])
+
+
+def test_batch_with_window_equals_exhaustive_masks():
+    tg.proposer_set(_params(12))
+    rng = np.random.default_rng(13)
+    vols = [torch.from_numpy(phantom.generate_host(phantom.chest_volume(50 + i, 160, 128, int(rng.integers(3, 20)),
+                                                                        vol_id=i))).cuda() for i in range(5)]
+    for mode in ("volume", "slice"):
+        m0, t0, _, _ = tg.tsallis_segment_batch(vols, tg.tsallis_params(q=0.8, mode=mode))
+        mk, tk, _, stk = tg.tsallis_segment_batch(vols, tg.tsallis_params(q=0.8, mode=mode, topk=64))
+        assert torch.equal(t0, tk)
+        for a, b in zip(m0, mk):
+            assert torch.equal(a, b)
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained weights in the package")
+def test_trained_proposer_narrows_the_search():
+    """Held-out 512x512 chest phantoms of the batch distribution (seeds not
+    used in training): with the trained weights the top-64 window holds the
+    exact threshold for most volumes and few blocks need an exhaustive
+    search; with an uninformed proposer (all weights zero: the window is
+    levels 0..63) the window never holds it and many blocks are searched.
+    Both give the exhaustive result."""
+    specs = phantom.batch_specs(777, nvol=24, dmin=120, dmax=600)
+    p = tg.tsallis_params(q=0.8, mode="volume")
+    h = torch.cat([tg.tsallis_histogram(phantom.generate_cuda(s), p) for s in specs])
+    res = {}
+    for name in ("trained", "uninformed"):
+        if name == "trained":
+            tg.proposer_load(WEIGHTS)
+        else:
+            tg.proposer_set(np.zeros(mlp.NPARAM, np.float32))
+        t0, _, _, tk, _, stk = _window_vs_exhaustive(h, 0.8)
+        assert np.array_equal(t0, tk)
+        res[name] = (float(((stk & tg.TSALLIS_STATUS_WINDOW_HIT) != 0).mean()),
+                     float(((stk >> tg.TSALLIS_STATUS_FALLBACK_SHIFT) & 0xff).mean()))
+    print("window hit rate, mean blocks searched:", res)
+    assert res["trained"][0] >= 0.75, res
+    assert res["uninformed"][0] == 0.0
+    assert res["trained"][1] < res["uninformed"][1], res
