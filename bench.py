@@ -249,29 +249,17 @@ def batch_leg(dev, steps=20, warmup=3):
            "autotuned": {"tile_vox": tile, "blocks_per_sm": bps, "ms": tune_ms},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "bytes_per_voxel": BATCH_BYTES_PER_VOXEL}}
-    res["proposer"] = proposer_leg(dev, vols, masks, outs)
+    res["proposer"] = proposer_legs(dev, vols, masks, outs, outs[0].clone())
     tg.set_launch_shape(65536, 0)
     del vols, masks, g
     torch.cuda.empty_cache()
     return res
 
 
-def proposer_leg(dev, vols, masks, outs, steps=10, warmup=3):
-    """The 64-volume batch with the trained proposer: histograms, the
-    proposer's top-64 window with its certificate and fallback, then
-    Algorithm 1. Reports voxels/s, how often the window held the maximiser,
-    how many 64-level blocks were searched, and the thresholds that differ
-    from the exhaustive path's (must be none)."""
+def _time_batch(dev, vols, p, masks, outs, steps, warmup):
     import torch
 
     import paper_2012_10684_gb300 as tg
-    weights = os.path.join(ROOT, "paper_2012_10684_gb300", "proposer_weights.bin")
-    if not os.path.exists(weights):
-        return {"unavailable": "no trained proposer weights in the package"}
-    tg.proposer_load(weights, dev)
-    nvox = sum(v.numel() for v in vols)
-    p = tg.tsallis_params(q=Q, mode="volume", topk=64)
-    ref_t = outs[0].clone()
     for _ in range(warmup):
         tg.tsallis_segment_batch(vols, p, masks, outs)
     torch.cuda.synchronize(dev)
@@ -283,15 +271,45 @@ def proposer_leg(dev, vols, masks, outs, steps=10, warmup=3):
         tg.tsallis_segment_batch(vols, p, masks, outs)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / steps
-    st = outs[2].cpu()
-    hit = ((st & tg.TSALLIS_STATUS_WINDOW_HIT) != 0).float().mean().item()
-    blocks = ((st >> tg.TSALLIS_STATUS_FALLBACK_SHIFT) & 0xff).float().mean().item()
-    misses = int((outs[0] != ref_t).sum().item())
-    return {"workload": "the batch above with the trained proposer, top-64 window, certified fallback",
-            "value": nvox / (ms / 1e3), "unit": "voxels/s", "ms_per_step": ms, "steps": steps,
-            "launches_per_step": 7, "window_hit_rate": hit, "mean_blocks_searched_of_64": blocks,
-            "threshold_misses_after_fallback": misses}
+    return e0.elapsed_time(e1) / steps
+
+
+def proposer_legs(dev, vols, masks, outs, ref_t, steps=10, warmup=3):
+    """The 64-volume batch with the trained proposer, two ways:
+    - window: histograms, the proposer's top-64 window with its certificate
+      and fallback, then Algorithm 1 (the volume read twice);
+    - first pass: the proposer predicts each volume's threshold from the
+      histogram of its middle sixteenth, the histogram pass binarises with
+      it and lists voxels within 8 levels; volumes whose exact threshold is
+      within 8 levels are finished by rewriting listed voxels, others are
+      binarised again;
+    and, for comparison, the first pass with the prediction taken from the
+    exhaustive search of the same sixteenth (no proposer).
+    Each reports voxels/s and the thresholds that differ from the exhaustive
+    path's (must be none)."""
+    import paper_2012_10684_gb300 as tg
+    weights = os.path.join(ROOT, "paper_2012_10684_gb300", "proposer_weights.bin")
+    if not os.path.exists(weights):
+        return {"unavailable": "no trained proposer weights in the package"}
+    tg.proposer_load(weights, dev)
+    nvox = sum(v.numel() for v in vols)
+    out = {}
+    legs = (("window", tg.tsallis_params(q=Q, mode="volume", topk=64)),
+            ("first_pass_proposer", tg.tsallis_params(q=Q, mode="volume", flags=tg.TSALLIS_FLAG_PREDICT_PROPOSER)),
+            ("first_pass_subsample", tg.tsallis_params(q=Q, mode="volume",
+                                                       flags=tg.TSALLIS_FLAG_PREDICT_SUBSAMPLE)))
+    for name, p in legs:
+        ms = _time_batch(dev, vols, p, masks, outs, steps, warmup)
+        st = outs[2].cpu()
+        r = {"value": nvox / (ms / 1e3), "unit": "voxels/s", "ms_per_step": ms, "steps": steps,
+             "threshold_misses_after_fallback": int((outs[0] != ref_t).sum().item())}
+        if name == "window":
+            r["window_hit_rate"] = ((st & tg.TSALLIS_STATUS_WINDOW_HIT) != 0).float().mean().item()
+            r["mean_blocks_searched_of_64"] = ((st >> tg.TSALLIS_STATUS_FALLBACK_SHIFT) & 0xff).float().mean().item()
+        else:
+            r["volumes_without_second_read"] = int(((st & tg.TSALLIS_STATUS_FIRST_PASS_EXACT) != 0).sum().item())
+        out[name] = r
+    return out
 
 
 def main():

@@ -77,6 +77,18 @@ typedef enum {
 /* Debug flags (tests only). */
 #define TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL 0x1u /* the first histogram tile never reports
                                                 arrival, so waits on its histogram run out */
+/* tsallis_segment_batch, whole-volume mode: binarise in the histogram pass
+ * with a threshold predicted from the histogram of the middle sixteenth of
+ * each volume's slices, by the proposer (PREDICT_PROPOSER; needs one, see
+ * tsallis_proposer_set) or by the exhaustive search of that histogram
+ * (PREDICT_SUBSAMPLE). When no voxel of a volume has a level between the
+ * predicted and the exact threshold, the mask written in the histogram pass
+ * is kept (3 bytes per voxel plus the sixteenth, instead of 5); otherwise the
+ * volume is binarised again. Results are those of the exhaustive path; only
+ * the memory traffic changes. Statuses of volumes finished without a second
+ * read carry TSALLIS_STATUS_FIRST_PASS_EXACT. */
+#define TSALLIS_FLAG_PREDICT_PROPOSER 0x2u
+#define TSALLIS_FLAG_PREDICT_SUBSAMPLE 0x4u
 
 typedef struct {
     int32_t lo;       /* Hounsfield value of level 0, -32768..32767; default -1024 */

@@ -23,6 +23,7 @@ struct tsallis_ctx {
     size_t scratch_bytes = 0;
     long long cap_groups = 0;
     long long cap_tiles = 0;
+    long long cap_exc = 0;
     unsigned long long timeout_ns = 1000000000ull;
     // launch shape of the 1-D persistent kernel
     int copies = 1;
@@ -57,6 +58,10 @@ struct tsallis_ctx {
     float* prop_x = nullptr;        // [prop_cap][256]
     int32_t* prop_cand = nullptr;   // [prop_cap][256]
     int prop_cap = 0;
+    // first-pass prediction of batches: sub-volume group table, histograms,
+    // predicted thresholds and the search's other outputs
+    void* pred_buf = nullptr;
+    int pred_cap = 0;
 };
 
 namespace {
@@ -95,7 +100,8 @@ tsallis_status check_params(const tsallis_params* p) {
         if (p->nbins & ((1 << p->shift) - 1)) return TSALLIS_ERR_INVALID_ARG;   // grey levels must fill [0, L2)
     }
     if (p->topk < 0) return TSALLIS_ERR_INVALID_ARG;
-    if (p->flags & ~TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL) return TSALLIS_ERR_INVALID_ARG;
+    if (p->flags & ~(TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL | TSALLIS_FLAG_PREDICT_PROPOSER | TSALLIS_FLAG_PREDICT_SUBSAMPLE))
+        return TSALLIS_ERR_INVALID_ARG;
     return TSALLIS_OK;
 }
 
@@ -108,13 +114,14 @@ tsallis_status check_shape(int64_t nx, int64_t ny, int64_t nz) {
     return TSALLIS_OK;
 }
 
-// Grows the context's scratch so it holds at least ngroups groups and
-// ntiles work tiles. The layout depends only on the capacities (arrive,
-// done_flag, bdone [capg]; that [capg]; ghist [capg][kMaxLevels]; bq [capt];
-// exc_n [capg]; exc [capg][kExcCap]), so state
-// left by one launch lines up with the next. New memory is zeroed; the
-// kernels keep it consistent between launches.
-size_t scratch_layout(long long capg, long long capt, size_t* ghist_off, size_t* bq_off, size_t* exc_off = nullptr) {
+// Grows the context's scratch so it holds at least ngroups groups, ntiles
+// work tiles and nexc first-pass exception entries. The layout depends only
+// on the capacities (arrive, done_flag, bdone [capg]; that [capg]; ghist
+// [capg][kMaxLevels]; bq [capt]; exc_n [capg]; exc [capx]), so state left
+// by one launch lines up with the next. New memory is zeroed; the kernels
+// keep it consistent between launches.
+size_t scratch_layout(long long capg, long long capt, long long capx, size_t* ghist_off, size_t* bq_off,
+                      size_t* exc_off) {
     size_t off = sizeof(ScratchHeader) + (size_t)capg * (3 * sizeof(int) + sizeof(unsigned long long));
     off = (off + 255) & ~size_t(255);
     if (ghist_off) *ghist_off = off;
@@ -123,16 +130,20 @@ size_t scratch_layout(long long capg, long long capt, size_t* ghist_off, size_t*
     if (bq_off) *bq_off = off;
     off += (size_t)capt * sizeof(unsigned long long);
     off = (off + 255) & ~size_t(255);
-    if (exc_off) *exc_off = off;   // exc_n [capg], then exc [capg][kExcCap]
-    return off + (size_t)capg * sizeof(int) + (size_t)capg * kExcCap * sizeof(unsigned);
+    if (exc_off) *exc_off = off;   // exc_n [capg], then the pool
+    off += (size_t)capg * sizeof(int);
+    off = (off + 255) & ~size_t(255);
+    return off + (size_t)capx * sizeof(unsigned long long);
 }
 
-tsallis_status ensure_scratch(tsallis_ctx* c, long long ngroups, long long ntiles) {
-    if (c->scratch && ngroups <= c->cap_groups && ntiles <= c->cap_tiles) return TSALLIS_OK;
+tsallis_status ensure_scratch(tsallis_ctx* c, long long ngroups, long long ntiles, long long nexc = 0) {
+    if (c->scratch && ngroups <= c->cap_groups && ntiles <= c->cap_tiles && nexc <= c->cap_exc) return TSALLIS_OK;
     long long capg = c->cap_groups > 0 ? c->cap_groups : 16;
     long long capt = c->cap_tiles > 0 ? c->cap_tiles : 4096;
+    long long capx = c->cap_exc;
     while (capg < ngroups) capg *= 2;
     while (capt < ntiles) capt *= 2;
+    if (capx < nexc) capx = nexc;
     if (c->scratch) {
         if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
         cudaFree(c->scratch);
@@ -140,8 +151,9 @@ tsallis_status ensure_scratch(tsallis_ctx* c, long long ngroups, long long ntile
         c->scratch_bytes = 0;
         c->cap_groups = 0;
         c->cap_tiles = 0;
+        c->cap_exc = 0;
     }
-    const size_t bytes = scratch_layout(capg, capt, nullptr, nullptr);
+    const size_t bytes = scratch_layout(capg, capt, capx, nullptr, nullptr, nullptr);
     if (cudaMalloc(&c->scratch, bytes) != cudaSuccess) {
         cudaGetLastError();
         return TSALLIS_ERR_OOM;
@@ -150,8 +162,12 @@ tsallis_status ensure_scratch(tsallis_ctx* c, long long ngroups, long long ntile
     c->scratch_bytes = bytes;
     c->cap_groups = capg;
     c->cap_tiles = capt;
+    c->cap_exc = capx;
     return TSALLIS_OK;
 }
+
+// Exception entries a first pass needs: 1/32 of the voxels its tiles span.
+inline long long exc_entries(long long ntiles, int tile_vox) { return (ntiles * (long long)tile_vox) >> 5; }
 
 // The term table for groups of n voxels at q: reused while n and q stay
 // the same, else rebuilt on the stream (ordered before the kernel that reads
@@ -285,13 +301,13 @@ struct ScratchView {
     int* ghist;
     unsigned long long* bq;
     int* exc_n;
-    unsigned* exc;
+    unsigned long long* exc;
 };
 
 ScratchView view(tsallis_ctx* c) {
     char* b = (char*)c->scratch;
     size_t goff = 0, qoff = 0, eoff = 0;
-    scratch_layout(c->cap_groups, c->cap_tiles, &goff, &qoff, &eoff);
+    scratch_layout(c->cap_groups, c->cap_tiles, c->cap_exc, &goff, &qoff, &eoff);
     ScratchView v;
     v.hdr = (ScratchHeader*)b;
     v.arrive = (int*)(b + sizeof(ScratchHeader));
@@ -301,7 +317,7 @@ ScratchView view(tsallis_ctx* c) {
     v.ghist = (int*)(b + goff);
     v.bq = (unsigned long long*)(b + qoff);
     v.exc_n = (int*)(b + eoff);
-    v.exc = (unsigned*)(v.exc_n + c->cap_groups);
+    v.exc = (unsigned long long*)(b + ((eoff + (size_t)c->cap_groups * sizeof(int) + 255) & ~size_t(255)));
     return v;
 }
 
@@ -550,6 +566,7 @@ void tsallis_destroy(tsallis_ctx* c) {
         if (c->mlp_params) cudaFree(c->mlp_params);
         if (c->mlp_act) cudaFree(c->mlp_act);
         if (c->prop_x) cudaFree(c->prop_x);
+        if (c->pred_buf) cudaFree(c->pred_buf);
     }
     delete c;
 }
@@ -722,7 +739,10 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
         const int ncl = (int)(nz < c->cluster_max ? nz : c->cluster_max);
         return cuda_status(launch_slice_cluster(a, ncl, stream));
     }
-    if ((st = ensure_scratch(c, ng, ng * ((gvox + c->tile_vox - 1) / c->tile_vox))) != TSALLIS_OK) return st;
+    const long long ntiles_all = ng * ((gvox + c->tile_vox - 1) / c->tile_vox);
+    if ((st = ensure_scratch(c, ng, ntiles_all, c->speculate ? exc_entries(ntiles_all, c->tile_vox) : 0)) !=
+        TSALLIS_OK)
+        return st;
     SegArgs a;
     fill_common(a, p, c);
     a.vol = d_vol;
@@ -742,8 +762,7 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
     a.spec = c->speculate;
     a.exc = v.exc;
     a.exc_n = v.exc_n;
-    a.exc_cap = kExcCap;
-    a.exc_w = gvox <= (1ll << 20) ? kExcWindow : 0;   // positions are kept in 20 bits
+    a.exc_w = c->speculate ? kExcWindow : 0;
     if (p->mode == TSALLIS_PER_SLICE) {
         a.ptab = pow_table(c, gvox, p->q, stream);
         a.ptab_n = gvox;
@@ -809,7 +828,16 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
         }
         return TSALLIS_OK;
     }
-    if ((st = ensure_scratch(c, ng, ntot)) != TSALLIS_OK) return st;
+    const unsigned predict = p->flags & (TSALLIS_FLAG_PREDICT_PROPOSER | TSALLIS_FLAG_PREDICT_SUBSAMPLE);
+    if (predict && (p->mode != TSALLIS_WHOLE_VOLUME || p->topk > 0 ||
+                    ((predict & TSALLIS_FLAG_PREDICT_PROPOSER) && (!c->mlp_ready || p->nbins != kMlpOut))))
+        return TSALLIS_ERR_INVALID_ARG;
+    const bool spec = c->speculate || predict;
+    // exception lists only for the speculation setting: with a prediction per
+    // volume the first-pass mask is kept when it is exact as written (listing
+    // the voxels near the prediction cost more than the second reads it saved)
+    const bool lists = c->speculate && !predict;
+    if ((st = ensure_scratch(c, ng, ntot, lists ? exc_entries(ntot, c->tile_vox) : 0)) != TSALLIS_OK) return st;
     // the group table, written on the device (capturable in a CUDA graph)
     const size_t table = (size_t)ng * sizeof(GroupDesc);
     if (!c->batch_buf || c->batch_bytes < table) {
@@ -866,25 +894,94 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
             return TSALLIS_ERR_CUDA;
         return TSALLIS_OK;
     }
+    const int32_t* hints = nullptr;
+    if (predict) {
+        // predicted thresholds: the histogram of the middle sixteenth of each
+        // volume's slices, read by the proposer (or searched exactly)
+        const size_t tb = ((size_t)nvol * sizeof(GroupDesc) + 255) & ~size_t(255);
+        const size_t hb = (size_t)nvol * kMaxLevels * sizeof(int32_t);
+        const size_t need = tb + hb + 3 * (((size_t)nvol * 4 + 255) & ~size_t(255));
+        if (!c->pred_buf || (size_t)c->pred_cap < need) {
+            if (c->pred_buf) {
+                if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
+                cudaFree(c->pred_buf);
+                c->pred_buf = nullptr;
+            }
+            if (cudaMalloc(&c->pred_buf, need) != cudaSuccess) {
+                cudaGetLastError();
+                c->pred_cap = 0;
+                return TSALLIS_ERR_OOM;
+            }
+            c->pred_cap = (int)need;
+        }
+        char* pb = static_cast<char*>(c->pred_buf);
+        GroupDesc* sub = reinterpret_cast<GroupDesc*>(pb);
+        int32_t* sh = reinterpret_cast<int32_t*>(pb + tb);
+        const size_t vb = ((size_t)nvol * 4 + 255) & ~size_t(255);
+        int32_t* ht = reinterpret_cast<int32_t*>(pb + tb + hb);
+        float* hphi = reinterpret_cast<float*>(pb + tb + hb + vb);
+        int32_t* hst = reinterpret_cast<int32_t*>(pb + tb + hb + 2 * vb);
+        std::vector<BatchVolDesc> sd((size_t)nvol);
+        long long stot = 0;
+        for (int i = 0; i < nvol; ++i) {
+            const tsallis_volume& v = h_vols[i];
+            const long long slice = v.nx * v.ny;
+            const long long ns = v.nz / 16 > 0 ? v.nz / 16 : 1, z0 = (v.nz - ns) / 2;
+            const long long gv = ns * slice;
+            const long long nt = (gv + c->tile_vox - 1) / c->tile_vox;
+            sd[i] = BatchVolDesc{v.vol + z0 * slice, v.mask + z0 * slice, gv, 1, (int)nt, i, (int)stot};
+            stot += nt;
+        }
+        for (int i0 = 0; i0 < nvol; i0 += kExpandVols) {
+            ExpandArgs ea;
+            std::memset(&ea, 0, sizeof(ea));
+            ea.nvol = nvol - i0 < kExpandVols ? nvol - i0 : kExpandVols;
+            for (int k = 0; k < ea.nvol; ++k) ea.v[k] = sd[(size_t)(i0 + k)];
+            ea.ngroups = ea.nvol;
+            ea.out = sub;
+            if (launch_expand_groups(ea, stream) != cudaSuccess) return TSALLIS_ERR_CUDA;
+        }
+        SegArgs h;
+        fill_common(h, p, c);
+        h.groups = sub;
+        h.ngroups = nvol;
+        h.ntotal = (unsigned)stot;
+        h.phases = kPhaseHist;
+        h.hdr = view(c).hdr;
+        h.ghist = sh;
+        if (cudaMemsetAsync(sh, 0, hb, stream) != cudaSuccess ||
+            launch_segment1d(h, grid_for(c, h.ntotal), c->copies, stream) != cudaSuccess)
+            return TSALLIS_ERR_CUDA;
+        if (predict & TSALLIS_FLAG_PREDICT_PROPOSER) {
+            if ((st = ensure_mlp_act(c, nvol)) != TSALLIS_OK || (st = ensure_prop(c, nvol)) != TSALLIS_OK) return st;
+            if (mlp_features(sh, nvol, c->prop_x, stream) != cudaSuccess ||
+                mlp_forward(c->mlp, c->prop_x, nvol, stream) != cudaSuccess ||
+                mlp_topk(c->mlp.z3, nvol, 1, ht, stream) != cudaSuccess)
+                return TSALLIS_ERR_CUDA;
+        } else if (launch_search1d(sh, nvol, p->nbins, p->q, ht, hphi, hst, nullptr, c->df_tables, stream) !=
+                   cudaSuccess) {
+            return TSALLIS_ERR_CUDA;
+        }
+        hints = ht;
+    }
     SegArgs a;
     fill_common(a, p, c);
     a.groups = groups;
     a.ngroups = (int)ng;
     a.ntotal = (unsigned)ntot;
     a.phases = kPhaseHist | kPhaseSearch | kPhaseBin;
+    a.flags = p->flags & TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL;
     ScratchView sv = view(c);
     a.hdr = sv.hdr;
     a.arrive = sv.arrive;
     a.done_flag = sv.done_flag;
     a.bdone = sv.bdone;
     a.that = sv.that;
-    a.spec = c->speculate;
+    a.spec = spec;
+    a.hint = hints;
     a.exc = sv.exc;
     a.exc_n = sv.exc_n;
-    a.exc_cap = kExcCap;
-    bool small = true;
-    for (const BatchVolDesc& v : vd) small = small && v.gvox <= (1ll << 20);
-    a.exc_w = small ? kExcWindow : 0;
+    a.exc_w = lists ? kExcWindow : 0;
     if (p->mode == TSALLIS_PER_SLICE) {
         // slices of the first volume's size get the term table (others
         // compute their terms)

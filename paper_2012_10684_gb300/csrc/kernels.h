@@ -61,12 +61,13 @@ struct SegArgs {
                                // threshold the group's first pass binarised with
     int spec;               // 1: histogram tiles also binarise with a predicted threshold
     // exceptions of the first pass: voxels whose level lies within exc_w of the
-    // predicted threshold, (position in group << 12) | (level - (t^ - exc_w + 1)),
-    // at most exc_cap per group; exc_w = 0: none are kept
-    unsigned* exc;          // [ngroups][exc_cap]
-    int* exc_n;             // [ngroups] entries appended (> exc_cap: overflowed)
-    int exc_cap;
+    // predicted threshold, (position in group << 16) | (level - (t^ - exc_w + 1));
+    // group g owns the pool entries from (first tile * tile_vox) / 32 on, as
+    // many as 1/32 of the voxels its tiles span; exc_w = 0: none are kept
+    unsigned long long* exc;
+    int* exc_n;             // [ngroups] entries appended (more than the region: overflowed)
     int exc_w;
+    const int* hint;        // optional [ngroups]: predicted thresholds (else the latest found)
     unsigned long long* bq; // [ntotal] binarise queue (launch tag | group | tile)
     int* ghist;             // [ngroups][L]: histogram target (scratch or caller's)
     const int* t_in;        // binarise-only: caller's thresholds
@@ -119,7 +120,6 @@ cudaError_t segment1d_prepare();
 // Term table of the table search for groups of n_max voxels, on stream s.
 cudaError_t build_pow_table(float2* tab, long long n_max, float q, const void* tables, cudaStream_t s);
 constexpr long long kPowTableMax = 1ll << 22;   // largest group size given a term table
-constexpr int kExcCap = 8192;      // first-pass exceptions kept per group
 constexpr int kExcWindow = 8;      // levels on each side of the predicted threshold
 
 // Per-slice 1-D form with the slice held in a cluster's shared memory

@@ -29,7 +29,7 @@ namespace tsl {
 
 constexpr int kSegThreads = kSearchThreads;  // 512
 constexpr int kSegMinBlocks = 2;
-constexpr int kExcSmem = kMaxBins * 2;   // a tile's exceptions held in shared memory (in the search's sT)
+constexpr int kExcSmem = kMaxBins * 2;   // a tile's exceptions held in shared memory (in the search's sT and sIC)
 
 __device__ __forceinline__ long long lmin(long long a, long long b) { return a < b ? a : b; }
 
@@ -97,9 +97,9 @@ __device__ __forceinline__ int bin_threshold(int t, int lo, int L, int shift) {
 
 // First-pass exceptions: voxels whose (clamped) value lies in [wlo, whi],
 // the window of levels around the predicted threshold, are appended to a
-// shared-memory list as (position in group << 12) | (level - wbase).
+// shared-memory list as (position in group << 16) | (level - wbase).
 struct ExcCtx {
-    unsigned* list;     // shared memory
+    unsigned long long* list;   // shared memory
     int* n;             // shared counter
     int cap;
     unsigned wlo2, whi2;   // window bounds as packed 16x2 values
@@ -112,11 +112,14 @@ struct ExcCtx {
 __device__ __forceinline__ void exc_append1(const ExcCtx& e, long long pos, int c) {
     if (c >= e.wlo && c <= e.whi) {
         const int k = atomicAdd(e.n, 1);
-        if (k < e.cap) e.list[k] = ((unsigned)pos << 12) | (unsigned)(c - e.lo - e.wbase);
+        if (k < e.cap) e.list[k] = ((unsigned long long)pos << 16) | (unsigned)(c - e.lo - e.wbase);
     }
 }
 
-// The exceptions among 8 clamped voxels (4 packed words) at group position pos.
+// The exceptions among 8 clamped voxels (4 packed words) at group position
+// pos. The lanes of a warp reserve their entries with one shared atomic
+// (each lane's offset is the sum of the counts of the lower active lanes,
+// built from ballots of the count's bits).
 __device__ __forceinline__ void exc_append8(const ExcCtx& e, const unsigned (&cl)[4], long long pos) {
     unsigned bits = 0;
 #pragma unroll
@@ -124,14 +127,28 @@ __device__ __forceinline__ void exc_append8(const ExcCtx& e, const unsigned (&cl
         const unsigned m = __vcmpges2(cl[j], e.wlo2) & __vcmples2(cl[j], e.whi2);
         bits |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * j);
     }
-    if (bits == 0) return;
-    int k = atomicAdd(e.n, __popc(bits));
+    const unsigned act = __activemask();
+    if (__any_sync(act, bits != 0) == 0) return;
+    const unsigned cnt = __popc(bits);
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned off = 0, tot = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const unsigned bal = __ballot_sync(act, (cnt >> b) & 1u);
+        off += (unsigned)__popc(bal & lt) << b;
+        tot += (unsigned)__popc(bal) << b;
+    }
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(e.n, (int)tot);
+    int k = __shfl_sync(act, base, leader) + (int)off;
     while (bits) {
         const int b = __ffs(bits) - 1;
         bits &= bits - 1;
         const unsigned w = cl[b >> 1];
         const int c = (b & 1) ? ((int)w >> 16) : (int)(short)(w & 0xffffu);
-        if (k < e.cap) e.list[k] = ((unsigned)(pos + b) << 12) | (unsigned)(c - e.lo - e.wbase);
+        if (k < e.cap) e.list[k] = ((unsigned long long)(pos + b) << 16) | (unsigned)(c - e.lo - e.wbase);
         ++k;
     }
 }
@@ -305,6 +322,17 @@ __device__ __forceinline__ int group_hint(const SegArgs& a, int epoch, int g) {
 }
 
 constexpr int kNoopTile = 0xfffff;   // queue entry of a group whose first-pass mask is exact
+constexpr int kPatchItem = 0x80000;  // queue entry: rewrite a share of the group's listed voxels
+
+// A group's region of the exception pool: 1/32 of the voxels its tiles span,
+// at the offset of its first tile (so regions never overlap).
+__device__ __forceinline__ long long exc_off_of(const SegArgs& a, int g) {
+    const long long t0 = a.groups != nullptr ? a.groups[g].tile_off : (long long)g * a.ntiles;
+    return (t0 * a.tile_vox) >> 5;
+}
+__device__ __forceinline__ long long exc_cap_of(const SegArgs& a, int g) {
+    return ((long long)group_tiles(a, g) * a.tile_vox) >> 5;
+}
 
 // Per-block scheduler state (lane 0 of the scheduler warp).
 struct SchedState {
@@ -423,7 +451,8 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
     __shared__ int s_last;
     __shared__ int s_any;
     __shared__ int s_exc_n, s_exc_cnt, s_exc_base, s_hint;
-    unsigned* sexc = reinterpret_cast<unsigned*>(sT);   // a tile's exceptions (the search's scratch is free then)
+    // a tile's exceptions (the search's scratch, sT and sIC, is free then)
+    unsigned long long* sexc = reinterpret_cast<unsigned long long*>(sT);
     const int tid = threadIdx.x;
     const int epoch = *(volatile int*)&a.hdr->epoch;
 
@@ -465,8 +494,18 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
             const long long off = (long long)w.tile * a.tile_vox;
             const long long n = lmin((long long)a.tile_vox, gn - off);
             if (w.kind == 1 && a.spec) {
-                // the group's predicted threshold, fixed by its first tile to start
-                if (tid == 0) s_hint = group_hint(a, epoch, w.group);
+                // the group's predicted threshold: given per group, or fixed by
+                // its first tile to start
+                if (tid == 0) {
+                    if (a.hint != nullptr) {
+                        const int hh = a.hint[w.group];
+                        *(volatile unsigned long long*)&a.that[w.group] =
+                            ((unsigned long long)(unsigned)(epoch + 1) << 32) | (unsigned)(hh + 1);
+                        s_hint = hh;
+                    } else {
+                        s_hint = group_hint(a, epoch, w.group);
+                    }
+                }
                 work_sync();
                 w.t = s_hint;
             }
@@ -504,14 +543,17 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                         const int ne = s_exc_n;
                         s_exc_n = 0;
                         s_exc_cnt = ne;
-                        s_exc_base = ne > kExcSmem ? atomicAdd(&a.exc_n[w.group], a.exc_cap + 1)   // overflow
+                        // a tile list that overflowed shared memory marks the group
+                        // as overflowed (bit 30: the count then exceeds any region)
+                        s_exc_base = ne > kExcSmem ? atomicOr(&a.exc_n[w.group], 0x40000000)
                                                    : atomicAdd(&a.exc_n[w.group], ne);
                     }
                     work_sync();
                     const int ne = s_exc_cnt, eb = s_exc_base;
-                    unsigned* gl = a.exc + (long long)w.group * a.exc_cap;
+                    const long long cap = exc_cap_of(a, w.group);
+                    unsigned long long* gl = a.exc + exc_off_of(a, w.group);
                     if (ne <= kExcSmem)
-                        for (int k = tid; k < ne && eb + k < a.exc_cap; k += kSegThreads) gl[eb + k] = sexc[k];
+                        for (int k = tid; k < ne && eb + k < cap; k += kSegThreads) gl[eb + k] = sexc[k];
                 }
                 // add the block histogram to the group's, leave sh zeroed
                 int* gh = a.ghist + (long long)w.group * a.L;
@@ -543,7 +585,7 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                         // the first pass binarised with a predicted threshold t^:
                         // its mask is exact when no voxel has a level between
                         // t^ and t (no voxel changes side)
-                        bool exact = false;
+                        bool exact = false, patch = false;
                         if (a.spec) {
                             const unsigned long long hv = *(volatile unsigned long long*)&a.that[w.group];
                             const int th = (hv >> 32) == (unsigned long long)(unsigned)(epoch + 1)
@@ -557,22 +599,14 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                                 if (any) s_any = 1;
                                 work_sync();
                                 exact = s_any == 0;
-                                const int ne = a.exc_w > 0 ? *(volatile int*)&a.exc_n[w.group] : 0;
+                                const long long ne = a.exc_w > 0 ? *(volatile int*)&a.exc_n[w.group] : 0;
                                 const int dt = r.t - th;
-                                if (!exact && a.exc_w > 0 && dt >= -a.exc_w && dt <= a.exc_w && ne <= a.exc_cap) {
-                                    // every voxel that changes side has a level in
-                                    // (b0 - 1, b1], inside the window: it is listed,
-                                    // so Algorithm 1 at t is applied to those voxels
-                                    const unsigned* gl = a.exc + (long long)w.group * a.exc_cap;
-                                    const int wbase = th - a.exc_w + 1;
-                                    const bool le = a.polarity == 0;
-                                    for (int k = tid; k < ne; k += kSegThreads) {
-                                        const unsigned e = __ldcg(gl + k);
-                                        const int lev = (int)(e & 0xfffu) + wbase;
-                                        if (lev >= b0 && lev <= b1) gmask[e >> 12] = ((lev <= r.t) == le) ? 1 : 0;
-                                    }
-                                    exact = true;
-                                }
+                                // every voxel that changes side has a level in
+                                // (b0 - 1, b1]; inside the window it is listed, and
+                                // the group's work items rewrite the listed voxels
+                                patch = !exact && a.exc_w > 0 && dt >= -a.exc_w && dt <= a.exc_w &&
+                                        ne <= exc_cap_of(a, w.group);
+                                exact = exact || patch;
                             }
                         }
                         for (int b = tid; b < a.L; b += kSegThreads) gh[b] = 0;   // scratch left zeroed
@@ -582,9 +616,8 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                             a.phi_out[w.group] = r.phi;
                             a.status[w.group] = r.status | (exact ? TSALLIS_STATUS_FIRST_PASS_EXACT : 0);
                             a.arrive[w.group] = 0;
-                            if (a.exc_w > 0) a.exc_n[w.group] = 0;
                             a.done_flag[w.group] = epoch + 1;
-                            if (exact) atomicAdd(&a.bdone[w.group], nt);
+                            if (exact && !patch) atomicAdd(&a.bdone[w.group], nt);
                             if (r.t >= 0)
                                 *(volatile unsigned long long*)&a.hdr->latest =
                                     ((unsigned long long)(unsigned)(epoch + 1) << 32) | (unsigned)(r.t + 1);
@@ -599,9 +632,30 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                         // all work is done)
                         const int base = s_last;
                         for (int j = tid; j < nt; j += kSegThreads)
-                            st_release_u64(&a.bq[base + j], bq_pack(epoch, w.group, exact ? kNoopTile : nt - 1 - j));
+                            st_release_u64(&a.bq[base + j],
+                                           bq_pack(epoch, w.group,
+                                                   patch ? (kPatchItem | j) : exact ? kNoopTile : nt - 1 - j));
                     }
                 }
+            } else if (w.t != -2 && (w.tile & kPatchItem)) {
+                // rewrite a share of the group's listed voxels with Algorithm 1 at t
+                const int k = w.tile & (kPatchItem - 1);
+                const int nt = group_tiles(a, w.group);
+                const long long ne = *(volatile int*)&a.exc_n[w.group];
+                const long long per = (ne + nt - 1) / nt;
+                const long long e0 = (long long)k * per, e1 = lmin(ne, e0 + per);
+                const unsigned long long hv = *(volatile unsigned long long*)&a.that[w.group];
+                const int th = (int)(hv & 0xffffffffu) - 1;
+                const int wbase = th - a.exc_w + 1;
+                const int b0 = (th < w.t ? th : w.t) + 1, b1 = th < w.t ? w.t : th;
+                const bool le = a.polarity == 0;
+                const unsigned long long* gl = a.exc + exc_off_of(a, w.group);
+                for (long long e = e0 + tid; e < e1; e += kSegThreads) {
+                    const unsigned long long x = __ldcg(gl + e);
+                    const int lev = (int)(x & 0xffffu) + wbase;
+                    if (lev >= b0 && lev <= b1) gmask[x >> 16] = ((lev <= w.t) == le) ? 1 : 0;
+                }
+                if (tid == 0) atomicAdd(&a.bdone[w.group], 1);
             } else if (w.t != -2) {
                 bin_tile(gvol + off, gmask + off, n, w.t, a.lo, a.L, a.bin_shift, a.polarity, pol_drop);
                 if (tid == 0 && (a.phases & kPhaseSearch)) atomicAdd(&a.bdone[w.group], 1);
@@ -631,10 +685,8 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                     a.status[g] = 5; /* TSALLIS_ERR_TIMEOUT */
                 }
                 a.bdone[g] = 0;
-                if (err) {
-                    a.arrive[g] = 0;
-                    if (a.exc_w > 0) a.exc_n[g] = 0;
-                }
+                if (a.exc_w > 0) a.exc_n[g] = 0;
+                if (err) a.arrive[g] = 0;
             }
             if (err) {
                 // clear every group's histogram

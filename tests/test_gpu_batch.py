@@ -187,3 +187,63 @@ def test_batch_of_64_uneven_chest_volumes_full_size():
         for z in rng.integers(0, spec.nz, 3):
             assert np.array_equal(m[z].cpu().numpy(), oracle.binarize(vh[z], int(t_g[i]))), (i, z)
         del vh
+
+
+@pytest.mark.parametrize("predictor", ["subsample", "proposer"])
+def test_batch_predicted_first_pass_equals_exhaustive(predictor):
+    """Whole-volume batch binarised in the histogram pass with a threshold
+    predicted from the middle sixteenth of each volume: thresholds, values
+    and masks equal those of the exhaustive path, and the volumes whose
+    prediction was close finish without a second read."""
+    import os
+    from oracle import mlp
+    weights = os.path.join(os.path.dirname(tg.__file__), "proposer_weights.bin")
+    if predictor == "proposer":
+        if os.path.exists(weights):
+            tg.proposer_load(weights)
+        else:
+            tg.proposer_set(np.zeros(mlp.NPARAM, np.float32))
+    flag = tg.TSALLIS_FLAG_PREDICT_PROPOSER if predictor == "proposer" else tg.TSALLIS_FLAG_PREDICT_SUBSAMPLE
+    vols_np = _uneven(19, 6, 256, 256, 24, 80)
+    vols = [torch.from_numpy(v).cuda() for v in vols_np]
+    m0, t0, phi0, st0 = tg.tsallis_segment_batch(vols, tg.tsallis_params(q=0.8, mode="volume"))
+    for rep in range(2):
+        mk, tk, phik, stk = tg.tsallis_segment_batch(vols, tg.tsallis_params(q=0.8, mode="volume", flags=flag))
+        torch.cuda.synchronize()
+        assert torch.equal(t0, tk) and torch.equal(phi0, phik)
+        assert torch.equal(st0 & 0xff, stk & 0xff)
+        for a, b in zip(m0, mk):
+            assert torch.equal(a, b)
+    first = ((stk.cpu().numpy() & tg.TSALLIS_STATUS_FIRST_PASS_EXACT) != 0)
+    print(predictor, "volumes finished in the first pass:", int(first.sum()), "of", len(first))
+    _check_batch(vols_np, "volume", 0.8)
+
+
+def test_batch_misleading_prediction_falls_back_exactly():
+    """Volumes whose middle slab differs from the rest (shifted values), so
+    the prediction from it is far from the exact threshold: the volumes are
+    binarised again and the results still equal the exhaustive path's."""
+    rng = np.random.default_rng(23)
+    vols_np = []
+    for i in range(4):
+        v = np.clip(rng.normal(-600, 200, (32, 96, 128)), -1024, 3071).astype(np.int16)
+        v[:, :30] = np.clip(rng.normal(100, 50, (32, 30, 128)), -1024, 3071).astype(np.int16)
+        v[15:17] = np.clip(v[15:17].astype(np.int32) + 700, -1024, 3071).astype(np.int16)   # the sampled slab
+        vols_np.append(v)
+    vols = [torch.from_numpy(v).cuda() for v in vols_np]
+    m0, t0, phi0, _ = tg.tsallis_segment_batch(vols, tg.tsallis_params(q=0.8, mode="volume"))
+    p = tg.tsallis_params(q=0.8, mode="volume", flags=tg.TSALLIS_FLAG_PREDICT_SUBSAMPLE)
+    mk, tk, phik, stk = tg.tsallis_segment_batch(vols, p)
+    torch.cuda.synchronize()
+    assert torch.equal(t0, tk) and torch.equal(phi0, phik)
+    for a, b in zip(m0, mk):
+        assert torch.equal(a, b)
+    assert not ((stk.cpu().numpy() & tg.TSALLIS_STATUS_FIRST_PASS_EXACT) != 0).all()
+
+
+def test_batch_prediction_argument_rules():
+    vols = [torch.zeros((2, 16, 16), dtype=torch.int16, device="cuda")]
+    for p in (tg.tsallis_params(mode="slice", flags=tg.TSALLIS_FLAG_PREDICT_SUBSAMPLE),
+              tg.tsallis_params(mode="volume", topk=64, flags=tg.TSALLIS_FLAG_PREDICT_SUBSAMPLE)):
+        with pytest.raises(tg.TsallisError):
+            tg.tsallis_segment_batch(vols, p)
