@@ -201,7 +201,7 @@ def cpu_baseline(vol_np, seconds=12.0):
                       "threads over slices), %.1f s" % (passes, dt)}
 
 
-def batch_leg(dev, steps=20, warmup=3):
+def batch_leg(dev, steps=20, warmup=3, nvol=64, dmax=600):
     """The 64-volume batch (512x512xD chest phantoms, D uniform in [120, 600],
     noise sd in [5, 30] HU, 4-8 airway generations, q = 0.8, one threshold
     per volume): autotuned launch shape, one persistent launch per step,
@@ -210,13 +210,13 @@ def batch_leg(dev, steps=20, warmup=3):
 
     import phantom
     import paper_2012_10684_gb300 as tg
-    specs = phantom.batch_specs(BATCH_SEED, nvol=64)
+    specs = phantom.batch_specs(BATCH_SEED, nvol=nvol, dmin=min(120, dmax), dmax=dmax)
     vols = [phantom.generate_cuda(sp, device=dev) for sp in specs]
     nvox = sum(v.numel() for v in vols)
     p = tg.tsallis_params(q=Q, mode="volume")
     masks = [torch.empty(v.shape, dtype=torch.uint8, device=dev) for v in vols]
-    outs = (torch.empty(64, dtype=torch.int32, device=dev), torch.empty(64, dtype=torch.float32, device=dev),
-            torch.empty(64, dtype=torch.int32, device=dev))
+    outs = (torch.empty(nvol, dtype=torch.int32, device=dev), torch.empty(nvol, dtype=torch.float32, device=dev),
+            torch.empty(nvol, dtype=torch.int32, device=dev))
     tile, bps, tune_ms = tg.tsallis_autotune_batch(vols, p, masks, outs)
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
@@ -243,7 +243,8 @@ def batch_leg(dev, steps=20, warmup=3):
     assert bool(((st & 0xff) == 0).all()), "a volume failed"
     peak, _ = _peaks()
     achieved = BATCH_BYTES_PER_VOXEL * nvox / (ms / 1e3) / 1e9
-    res = {"workload": "64 chest phantoms 512x512xD, D~U[120,600], noise sd U[5,30], q=0.8, per-volume thresholds",
+    res = {"workload": "%d chest phantoms 512x512xD, D~U[%d,%d], noise sd U[5,30], q=0.8, per-volume thresholds"
+                       % (nvol, min(120, dmax), dmax),
            "voxels": nvox, "value": nvox / (ms / 1e3), "unit": "voxels/s", "ms_per_step": ms, "steps": steps,
            "launch": "CUDA graph: group-table kernel + one persistent kernel",
            "autotuned": {"tile_vox": tile, "blocks_per_sm": bps, "ms": tune_ms},
@@ -320,6 +321,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-volume batch leg")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batch leg (for profiling; prints the leg's JSON object)")
+    ap.add_argument("--batch-nvol", type=int, default=64)
+    ap.add_argument("--batch-dmax", type=int, default=600)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -345,6 +350,11 @@ def main():
     import __graft_entry__
     if rank == 0 or world == 1:
         __graft_entry__.build()
+    if args.batch_only:
+        torch.cuda.set_device(local)
+        print(json.dumps(batch_leg(torch.device("cuda", local), nvol=args.batch_nvol, dmax=args.batch_dmax)),
+              flush=True)
+        return 0
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

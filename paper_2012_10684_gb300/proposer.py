@@ -2,11 +2,12 @@
 
 Data: seeded chest phantoms (512 x 512 x D, D uniform in [dmin, dmax], sensor
 noise sd uniform in [5, 30] HU, 4-8 airway generations), generated on the
-GPU one at a time. For each volume the 4096-level whole-volume histogram is
-computed (tsallis_histogram) and labelled with the exhaustive search's
-threshold (tsallis_search); the volume itself is not kept. The target of a
-histogram is the uniform distribution over the thresholds that give the
-labelled partition (the labelled level and the empty levels after it).
+GPU one at a time. For each volume the 4096-level whole-volume histogram and
+the histogram of its middle sixteenth of slices are computed
+(tsallis_histogram), and both are labelled with the exhaustive search's
+threshold of the whole volume (tsallis_search); the volume itself is not
+kept. The target is the uniform distribution over the thresholds that give
+the labelled partition (the labelled level and the empty levels after it).
 
 Training: Adam on the mean soft-target cross-entropy (the library's
 forward, backward and optimiser kernels), minibatches drawn with a seeded
@@ -41,11 +42,15 @@ def soft_targets(hist: torch.Tensor, t: torch.Tensor) -> torch.Tensor:
 
 def make_dataset(n: int, seed: int, dmin: int, dmax: int, q: float = 0.8, nx: int = 512, ny: int = 512,
                  device="cuda", log_every: int = 0):
-    """(hist [n][4096] int32, t [n] int32) from n generated volumes."""
+    """(hist [n][4096], sub [n][4096], t [n], status [n]) from n generated
+    volumes: each volume's histogram, the histogram of the middle sixteenth
+    of its slices (what a batch's first-pass prediction reads), and the
+    exhaustive search's threshold of the whole volume."""
     import phantom
     rng = np.random.default_rng(seed)
     p = tg.tsallis_params(q=q, mode="volume")
     hist = torch.empty((n, 4096), dtype=torch.int32, device=device)
+    sub = torch.empty((n, 4096), dtype=torch.int32, device=device)
     buf = torch.empty(dmax * ny * nx, dtype=torch.int16, device=device)
     t0 = time.time()
     for i in range(n):
@@ -55,10 +60,13 @@ def make_dataset(n: int, seed: int, dmin: int, dmax: int, q: float = 0.8, nx: in
         vol = buf[: nz * ny * nx].view(nz, ny, nx)
         phantom.generate_cuda(spec, out=vol)
         tg.tsallis_histogram(vol, p, hist[i:i + 1])
+        ns = max(1, nz // 16)
+        z0 = (nz - ns) // 2
+        tg.tsallis_histogram(vol[z0:z0 + ns], p, sub[i:i + 1])
         if log_every and (i + 1) % log_every == 0:
             print("generated %d volumes, %.1f s" % (i + 1, time.time() - t0), flush=True)
     t, _, st = tg.tsallis_search(hist, p)
-    return hist, t, st
+    return hist, sub, t, st
 
 
 def train(x: torch.Tensor, y: torch.Tensor, steps: int, batch: int, lr: float, seed: int, init_seed: int = 1,
@@ -92,7 +100,7 @@ def main():
     ap.add_argument("--volumes", type=int, default=20000)
     ap.add_argument("--dmin", type=int, default=120)
     ap.add_argument("--dmax", type=int, default=600)
-    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=2012106845)
@@ -102,10 +110,13 @@ def main():
     __graft_entry__.build()
     torch.cuda.set_device(0)
     t0 = time.time()
-    hist, t, st = make_dataset(args.volumes, args.seed, args.dmin, args.dmax, log_every=1000)
+    hist, sub, t, st = make_dataset(args.volumes, args.seed, args.dmin, args.dmax, log_every=1000)
     assert bool(((st & 0xff) == 0).all())
-    x = tg.proposer_features(hist)
+    # each volume gives two examples with the same target: its histogram
+    # (for the window search) and its middle sixteenth (for the prediction)
+    x = torch.cat([tg.proposer_features(hist), tg.proposer_features(sub)])
     y = soft_targets(hist, t)
+    y = torch.cat([y, y])
     torch.cuda.synchronize()
     t1 = time.time()
     losses = train(x, y, args.steps, args.batch, args.lr, args.seed, log_every=500)
