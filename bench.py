@@ -48,7 +48,7 @@ def _peaks():
 
 def _kernel_source_sha():
     h = hashlib.sha256()
-    for name in ("common.cuh", "dfmath.cuh", "search1d.cuh", "seg1d.cu", "kernels.h"):
+    for name in ("common.cuh", "dfmath.cuh", "top.cuh", "search1d.cuh", "seg1d.cu", "kernels.h"):
         with open(os.path.join(ROOT, "paper_2012_10684_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
