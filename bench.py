@@ -313,6 +313,45 @@ def proposer_legs(dev, vols, masks, outs, ref_t, steps=10, warmup=3):
     return out
 
 
+def two_d_leg(dev, steps=10, warmup=3):
+    """The 2-D form on a 512x512x256 chest phantom: grey level (4096 levels
+    >> 4) x 3x3x3 floor-mean level, 65,536-bin histogram, exhaustive (t, s)
+    search over summed-area tables with an FP64 re-rank of near ties,
+    Algorithm 1 on the grey level with t; one threshold pair for the volume.
+    Algorithmic bytes: 5 per voxel (the histogram pass reads the volume,
+    the binarise pass reads it again and writes the mask)."""
+    import torch
+
+    import phantom
+    import paper_2012_10684_gb300 as tg
+    vol = phantom.generate_cuda(phantom.chest_volume(2012106843, NX, NY, 256), device=dev)
+    p = tg.tsallis_params(q=Q, mode="volume", two_d=True)
+    mask = torch.empty(vol.shape, dtype=torch.uint8, device=dev)
+    t = torch.empty((1, 2), dtype=torch.int32, device=dev)
+    phi = torch.empty(1, dtype=torch.float32, device=dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    for _ in range(warmup):
+        tg.tsallis_segment(vol, p, mask, t, phi, st)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        tg.tsallis_segment(vol, p, mask, t, phi, st)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    assert int(st[0].item()) & 0xff == 0
+    peak, _ = _peaks()
+    achieved = 5 * vol.numel() / (ms / 1e3) / 1e9
+    return {"workload": "chest phantom 512x512x256, 2-D grey x 3x3x3 mean, q=0.8, one (t, s) for the volume",
+            "value": vol.numel() / (ms / 1e3), "unit": "voxels/s", "ms_per_step": ms, "steps": steps,
+            "t_s": [int(x) for x in t[0].tolist()],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_voxel": 5}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,6 +490,7 @@ def main():
         "rerank_slices": int(((status & tg.TSALLIS_STATUS_RERANKED) != 0).sum()),
     }
     if not args.no_batch:
+        line["two_d"] = two_d_leg(dev)
         line["batch"] = batch_leg(dev)
         line["gpu_launches_batch"] = 2 * line["batch"]["steps"]
     if not args.no_cpu_baseline and world >= 1:
