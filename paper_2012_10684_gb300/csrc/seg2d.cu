@@ -26,18 +26,20 @@
 //               [0..t] x [0..s]) and suffix over rows of the row suffixes
 //               (sums over [t..] x [s..]); quadrant-2 sums are accumulated
 //               from their own corner, never as a total minus quadrant 1;
-//   k_s2_eval   phi(t, s) in FP32 with its error bound for every pair, and
-//               per row t the best entry and the largest phi + error;
-//   k_s2_final  the FP32 maximum and its error band; every pair whose band
-//               reaches it is re-evaluated in FP64 from the double-float
-//               sums; the FP64 maximiser wins, and among pairs with its
-//               partition (the same quadrant counts) and the same value the
-//               smallest (t, s) is returned.
+//   k_s2_eval   phi(t, s) in double-float with its error bound for every
+//               pair, and per row t the row's running top (its best pair,
+//               and the largest value + bound among the others);
+//   k_s2_final  the maximum over the rows' tops; when another pair's bound
+//               reaches it, the pairs inside the bounds are re-evaluated in
+//               FP64 from the double-float sums, the FP64 maximiser wins, and
+//               among pairs with its partition (the same quadrant counts) and
+//               the same value the smallest (t, s) is returned.
 #include <cmath>
 
 #include "common.cuh"
 #include "dfmath.cuh"
 #include "kernels.h"
+#include "top.cuh"
 #include "../../include/tsallis.h"
 
 namespace tsl {
@@ -226,10 +228,14 @@ struct S2Args {
     float2* PW;           // terms, then quadrant-1 term sums
     int* SC;              // [K][L2][L2] counts, then quadrant-2 counts
     float2* SW;
-    float* rphi;          // [K][L2]: per row t, best FP32 phi
-    float* rerr;          //           its error bound
-    float* rupper;        //           largest phi + error
-    int* rs;              //           its s (-1: no valid pair in the row)
+    // per row t, the row's running top (top.cuh): its best value (double-
+    // float), the pair index t * (L2 - 1) + s (-1: no valid pair), its error
+    // bound, and the largest value + bound among the row's other pairs
+    float* rvh;           // [K][L2]
+    float* rvl;
+    float* rband;
+    float* ru2;
+    int* ri;
     float* curve;         // optional [K][L2-1][L2-1]
     int* t_out;           // [K][2] (t, s)
     int* t_bin;           // optional [K]: t alone, for the binarise pass
@@ -297,53 +303,72 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_rows(const S2Args a) {
     if (s < a.L2) { a.SC[o + s] = c; a.SW[o + s] = make_float2(ws.hi, ws.lo); }
 }
 
-// Column scans: 32 columns x 8 row chunks per block.
-__global__ void __launch_bounds__(256) k_s2_cols(const S2Args a) {
-    __shared__ int tcA[8][32], tcB[8][32];
-    __shared__ F2 twA[8][32], twB[8][32];
+// Column scans: 32 columns x 32 row chunks per block (at most 8 rows per
+// chunk for L2 <= 256). Each thread loads its chunk's cells together into
+// registers, the chunk totals are exchanged through shared memory (summed
+// in a fixed order), and the thread scans its chunk in registers: prefix
+// over rows of the row prefixes, suffix over rows of the row suffixes.
+constexpr int kColRows = 8;
+__global__ void __launch_bounds__(1024) k_s2_cols(const S2Args a) {
+    __shared__ int tcA[32][33], tcB[32][33];
+    __shared__ F2 twA[32][33], twB[32][33];
     const int c = threadIdx.x & 31, r = threadIdx.x >> 5;
     const int k = blockIdx.y, s = blockIdx.x * 32 + c;
-    const int rc = (a.L2 + 7) / 8, i0 = min(r * rc, a.L2), i1 = min(i0 + rc, a.L2);
+    const int rc = (a.L2 + 31) / 32, i0 = min(r * rc, a.L2), i1 = min(i0 + rc, a.L2);
     const long long o = s2_off(a, k);
-    int ca = 0, cb = 0;
-    F2 wa{0.f, 0.f}, wb{0.f, 0.f};
-    if (s < a.L2) {
-        for (int i = i0; i < i1; ++i) {
+    int pc[kColRows], sc[kColRows];
+    F2 pw[kColRows], sw[kColRows];
+#pragma unroll
+    for (int j = 0; j < kColRows; ++j) {
+        const int i = i0 + j;
+        pc[j] = 0; sc[j] = 0;
+        pw[j] = F2{0.f, 0.f}; sw[j] = F2{0.f, 0.f};
+        if (s < a.L2 && i < i1) {
             const long long e = o + (long long)i * a.L2 + s;
-            ca += a.PC[e];
-            const float2 x = a.PW[e];
-            wa = f2_add(wa, F2{x.x, x.y});
-        }
-        for (int i = i1 - 1; i >= i0; --i) {
-            const long long e = o + (long long)i * a.L2 + s;
-            cb += a.SC[e];
-            const float2 x = a.SW[e];
-            wb = f2_add(F2{x.x, x.y}, wb);
+            pc[j] = a.PC[e];
+            sc[j] = a.SC[e];
+            const float2 x = a.PW[e], y = a.SW[e];
+            pw[j] = F2{x.x, x.y};
+            sw[j] = F2{y.x, y.y};
         }
     }
+    int ca = 0, cb = 0;
+    F2 wa{0.f, 0.f}, wb{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < kColRows; ++j) { ca += pc[j]; wa = f2_add(wa, pw[j]); }
+#pragma unroll
+    for (int j = kColRows - 1; j >= 0; --j) { cb += sc[j]; wb = f2_add(sw[j], wb); }
     tcA[r][c] = ca; twA[r][c] = wa;
     tcB[r][c] = cb; twB[r][c] = wb;
     __syncthreads();
     ca = 0; cb = 0;
     wa = F2{0.f, 0.f}; wb = F2{0.f, 0.f};
     for (int j = 0; j < r; ++j) { ca += tcA[j][c]; wa = f2_add(wa, twA[j][c]); }
-    for (int j = 7; j > r; --j) { cb += tcB[j][c]; wb = f2_add(twB[j][c], wb); }
+    for (int j = 31; j > r; --j) { cb += tcB[j][c]; wb = f2_add(twB[j][c], wb); }
     if (s >= a.L2) return;
-    for (int i = i0; i < i1; ++i) {
-        const long long e = o + (long long)i * a.L2 + s;
-        ca += a.PC[e];
-        const float2 x = a.PW[e];
-        wa = f2_add(wa, F2{x.x, x.y});
-        a.PC[e] = ca;
-        a.PW[e] = make_float2(wa.hi, wa.lo);
+#pragma unroll
+    for (int j = 0; j < kColRows; ++j) {
+        ca += pc[j];
+        wa = f2_add(wa, pw[j]);
+        pc[j] = ca;
+        pw[j] = wa;
     }
-    for (int i = i1 - 1; i >= i0; --i) {
+#pragma unroll
+    for (int j = kColRows - 1; j >= 0; --j) {
+        cb += sc[j];
+        wb = f2_add(sw[j], wb);
+        sc[j] = cb;
+        sw[j] = wb;
+    }
+#pragma unroll
+    for (int j = 0; j < kColRows; ++j) {
+        const int i = i0 + j;
+        if (i >= i1) break;
         const long long e = o + (long long)i * a.L2 + s;
-        cb += a.SC[e];
-        const float2 x = a.SW[e];
-        wb = f2_add(F2{x.x, x.y}, wb);
-        a.SC[e] = cb;
-        a.SW[e] = make_float2(wb.hi, wb.lo);
+        a.PC[e] = pc[j];
+        a.PW[e] = make_float2(pw[j].hi, pw[j].lo);
+        a.SC[e] = sc[j];
+        a.SW[e] = make_float2(sw[j].hi, sw[j].lo);
     }
 }
 
@@ -358,29 +383,6 @@ __device__ __forceinline__ Quad quad_sums(const S2Args& a, int k, int t, int s) 
     const long long ea = o + (long long)t * a.L2 + s, eb = o + (long long)(t + 1) * a.L2 + (s + 1);
     const float2 x = a.PW[ea], y = a.SW[eb];
     return Quad{a.PC[ea], a.SC[eb], F2{x.x, x.y}, F2{y.x, y.y}};
-}
-
-// FP32 objective and its error bound (the 1-D bound: the class sums are
-// double-float sums rounded once). err < 0 marks an empty quadrant.
-__device__ __forceinline__ void eval32(const Quad& u, float q, const DfTables* T, float& f, float& err) {
-    f = 0.f;
-    err = -1.f;
-    if (u.na <= 0 || u.nb <= 0) return;
-    const float qa = f2_val(u.qa), qb = f2_val(u.qb);
-    const float fa = (float)u.na, fb = (float)u.nb;
-    if (q == 1.0f) {
-        const float ua = log2f(fa), ub = log2f(fb);
-        const float va = qa / fa, vb = qb / fb;
-        const float fbits = (ua - va) + (ub - vb);
-        f = 0.693147182f * fbits;
-        err = shannon_err(ua, va, ub, vb, fbits);
-    } else {
-        const F2 LN{kFixedLog2N, 0.f};
-        const float fN = 2147483648.0f;
-        const float ab = (qa / class_pow_f32<true>(u.na, fN, LN, q, T)) * (qb / class_pow_f32<true>(u.nb, fN, LN, q, T));
-        f = (1.0f - ab) / (q - 1.0f);
-        err = tsallis_err(ab, f, q);
-    }
 }
 
 __device__ __forceinline__ double eval64(const Quad& u, float q, const DfTables* T) {
@@ -405,56 +407,72 @@ struct RedSmem {
     int n[kS2Threads / 32];
 };
 
-__global__ void __launch_bounds__(kS2Threads) k_s2_eval(const S2Args a) {
-    __shared__ RedSmem sm;
-    const int k = blockIdx.y, t = blockIdx.x, s = threadIdx.x;
-    const int lane = s & 31, warp = s >> 5;
-    const int m = a.L2 - 1;
-    float f = 0.f, err = -1.f;
-    if (s < m) eval32(quad_sums(a, k, t, s), a.q, a.T, f, err);
-    if (a.curve && s < m) a.curve[((long long)k * m + t) * m + s] = err >= 0.f ? f : __int_as_float(0x7fc00000);
-    float bv = f, up = err >= 0.f ? f + err : -INFINITY;
-    int bi = err >= 0.f ? s : -1;
-    warp_argmax(bv, bi);
+// Double-float objective of a pair and its error bound (top.cuh); false
+// when a quadrant is empty.
+__device__ __forceinline__ bool eval_df(const Quad& u, float q, const DfTables* T, F2& phi, float& band) {
+    if (u.na <= 0 || u.nb <= 0) return false;
+    const F2 LN{kFixedLog2N, 0.f};
+    if (q == 1.0f) {
+        const F2 la = df_log2_count<true>((unsigned)u.na, T), lb = df_log2_count<true>((unsigned)u.nb, T);
+        const F2 sa = df_div(u.qa, df_from_u32((unsigned)u.na)), sb = df_div(u.qb, df_from_u32((unsigned)u.nb));
+        phi = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
+        band = shannon_band_df(la.hi, sa.hi, lb.hi, sb.hi);
+    } else {
+        const F2 pa = df_pow_ratio<true>((unsigned)u.na, LN, q, T), pb = df_pow_ratio<true>((unsigned)u.nb, LN, q, T);
+        const F2 ab = df_mul(df_div(u.qa, pa), df_div(u.qb, pb));
+        phi = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), two_sum(q, -1.0f));
+        band = tsallis_band_df(ab.hi, phi.hi, q);
+    }
+    return true;
+}
+
+// Per-warp tops, reduced by warp 0 into sm.t[0].
+struct TopSmem {
+    float vh[kS2Threads / 32], vl[kS2Threads / 32], band[kS2Threads / 32], u2[kS2Threads / 32];
+    int i[kS2Threads / 32];
+};
+__device__ Top block_top2(Top tp, TopSmem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) up = fmaxf(up, __shfl_xor_sync(0xffffffffu, up, d));
-    if (lane == 0) { sm.v[warp] = bv; sm.i[warp] = bi; sm.u[warp] = up; }
-    __syncthreads();
-    if (warp == 0) {
-        constexpr int kW = kS2Threads / 32;
-        bv = lane < kW ? sm.v[lane] : 0.f;
-        bi = lane < kW ? sm.i[lane] : -1;
-        up = lane < kW ? sm.u[lane] : -INFINITY;
-        warp_argmax(bv, bi);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) up = fmaxf(up, __shfl_xor_sync(0xffffffffu, up, d));
-        if (lane == 0) {
-            sm.i[0] = bi;
-            sm.v[0] = bv;
-            sm.u[0] = up;
-        }
+    for (int d = 16; d > 0; d >>= 1) tp = top_merge(tp, shfl_top(tp, d));
+    if (lane == 0) {
+        sm.vh[warp] = tp.v.hi; sm.vl[warp] = tp.v.lo; sm.band[warp] = tp.band; sm.u2[warp] = tp.u2; sm.i[warp] = tp.i;
     }
     __syncthreads();
-    const int best = sm.i[0];
-    if (s == best) a.rerr[(long long)k * a.L2 + t] = err;
+    Top g{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
+#pragma unroll
+    for (int w = 0; w < kS2Threads / 32; ++w) g = top_merge(g, Top{{sm.vh[w], sm.vl[w]}, sm.i[w], sm.band[w], sm.u2[w]});
+    __syncthreads();
+    return g;
+}
+
+// One block per row t: the objective at every (t, s) in double-float, and
+// the row's top.
+__global__ void __launch_bounds__(kS2Threads) k_s2_eval(const S2Args a) {
+    __shared__ TopSmem sm;
+    const int k = blockIdx.y, t = blockIdx.x, s = threadIdx.x;
+    const int m = a.L2 - 1;
+    Top tp{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
+    F2 phi{0.f, 0.f};
+    float band = 0.f;
+    bool ok = false;
+    if (s < m) {
+        ok = eval_df(quad_sums(a, k, t, s), a.q, a.T, phi, band);
+        if (ok) tp = Top{phi, t * m + s, band, -INFINITY};
+    }
+    if (a.curve && s < m) a.curve[((long long)k * m + t) * m + s] = ok ? phi.hi + phi.lo : __int_as_float(0x7fc00000);
+    const Top g = block_top2(tp, sm);
     if (s == 0) {
-        a.rphi[(long long)k * a.L2 + t] = sm.v[0];
-        a.rs[(long long)k * a.L2 + t] = best;
-        a.rupper[(long long)k * a.L2 + t] = sm.u[0];
+        const long long r = (long long)k * a.L2 + t;
+        a.rvh[r] = g.v.hi;
+        a.rvl[r] = g.v.lo;
+        a.rband[r] = g.band;
+        a.ru2[r] = g.u2;
+        a.ri[r] = g.i;
     }
 }
 
 // Block reductions for the final kernel.
-__device__ void red_argmax_f(float& v, int& i, RedSmem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    warp_argmax(v, i);
-    if (lane == 0) { sm.v[warp] = v; sm.i[warp] = i; }
-    __syncthreads();
-    v = lane < kS2Threads / 32 ? sm.v[lane] : 0.f;
-    i = lane < kS2Threads / 32 ? sm.i[lane] : -1;
-    warp_argmax(v, i);
-    __syncthreads();
-}
 __device__ void red_argmax_d(double& v, int& i, RedSmem& sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     warp_argmax(v, i);
@@ -475,34 +493,26 @@ __device__ int red_min_i(int v, RedSmem& sm) {
     __syncthreads();
     return v;
 }
-__device__ int red_sum_i(int v, RedSmem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = __reduce_add_sync(0xffffffffu, v);
-    if (lane == 0) sm.n[warp] = v;
-    __syncthreads();
-    v = lane < kS2Threads / 32 ? sm.n[lane] : 0;
-    v = __reduce_add_sync(0xffffffffu, v);
-    __syncthreads();
-    return v;
-}
-
 // Two FP64 values of one partition computed from differently associated
 // double-float sums agree to far better than this; distinct partitions
 // closer than this are near-ties.
 constexpr double kSamePartitionTol = 1e-10;
 
+// One block per histogram: the maximum over the rows' tops; when another
+// pair's bound reaches it, the pairs inside the bounds are re-ranked in FP64,
+// and among pairs with the winner's quadrant counts and value the smallest
+// (t, s) is returned.
 __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
+    __shared__ TopSmem tsm;
     __shared__ RedSmem sm;
     const int k = blockIdx.x, tid = threadIdx.x;
     const int m = a.L2 - 1;
     const long long ro = (long long)k * a.L2;
-    // 1. FP32 maximum over rows (rows are already reduced; smallest t wins ties)
-    float bv = 0.f;
-    int bt = -1;
+    Top tp{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
     for (int t = tid; t < m; t += kS2Threads)
-        if (a.rs[ro + t] >= 0) argmax_merge(bv, bt, a.rphi[ro + t], t);
-    red_argmax_f(bv, bt, sm);
-    if (bt < 0) {
+        tp = top_merge(tp, Top{{a.rvh[ro + t], a.rvl[ro + t]}, a.ri[ro + t], a.rband[ro + t], a.ru2[ro + t]});
+    const Top g = block_top2(tp, tsm);
+    if (g.i < 0) {
         if (tid == 0) {
             a.t_out[2 * k] = -1;
             a.t_out[2 * k + 1] = -1;
@@ -512,42 +522,53 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
         }
         return;
     }
-    const float lower = bv - a.rerr[ro + bt];
-    // 2. FP64 values of every pair inside the band; the FP64 maximiser
+    const float lower = g.v.hi - g.band;
+    if (!(g.u2 >= lower)) {
+        if (tid == 0) {
+            a.t_out[2 * k] = g.i / m;
+            a.t_out[2 * k + 1] = g.i % m;
+            if (a.t_bin) a.t_bin[k] = g.i / m;
+            a.phi_out[k] = g.v.hi + g.v.lo;
+            a.status[k] = TSALLIS_OK;
+        }
+        return;
+    }
+    // rows holding a pair inside the bounds (uniform over the block)
+    auto row_in = [&](int t) {
+        return a.ri[ro + t] >= 0 && (a.rvh[ro + t] + a.rband[ro + t] >= lower || a.ru2[ro + t] >= lower);
+    };
     double dv = 0.0;
-    int di = -1, nband = 0;
+    int di = -1;
     for (int t = 0; t < m; ++t) {
-        if (!(a.rupper[ro + t] >= lower)) continue;   // uniform over the block
+        if (!row_in(t)) continue;
         for (int s = tid; s < m; s += kS2Threads) {
             const Quad u = quad_sums(a, k, t, s);
-            float f, err;
-            eval32(u, a.q, a.T, f, err);
-            if (err >= 0.f && f + err >= lower) {
-                ++nband;
+            F2 phi;
+            float band;
+            if (eval_df(u, a.q, a.T, phi, band) && phi.hi + band >= lower)
                 argmax_merge(dv, di, eval64(u, a.q, a.T), t * m + s);
-            }
         }
     }
     red_argmax_d(dv, di, sm);
-    nband = red_sum_i(nband, sm);
-    if (di < 0) {   // the FP32 maximiser is always inside its own band; kept as a guard
-        di = bt * m + a.rs[ro + bt];
-        dv = eval64(quad_sums(a, k, bt, a.rs[ro + bt]), a.q, a.T);
+    if (di < 0) {   // the maximum is inside its own bound; kept as a guard
+        di = g.i;
+        dv = eval64(quad_sums(a, k, g.i / m, g.i % m), a.q, a.T);
     }
     const int wt = di / m, ws = di - wt * m;
     const Quad uw = quad_sums(a, k, wt, ws);
     const double tol = kSamePartitionTol * fmax(fabs(dv), 1.0);
-    // 3. canonical pair: the smallest (t, s) with the winner's partition and value
+    // canonical pair: the smallest (t, s) with the winner's partition and value
     int ci = 0x7fffffff;
     for (int t = 0; t < m && t <= wt; ++t) {
-        if (!(a.rupper[ro + t] >= lower)) continue;
+        if (!row_in(t)) continue;
         for (int s = tid; s < m; s += kS2Threads) {
             if (t * m + s >= di) break;
             const Quad u = quad_sums(a, k, t, s);
             if (u.na != uw.na || u.nb != uw.nb) continue;
-            float f, err;
-            eval32(u, a.q, a.T, f, err);
-            if (err >= 0.f && f + err >= lower && fabs(eval64(u, a.q, a.T) - dv) <= tol) ci = min(ci, t * m + s);
+            F2 phi;
+            float band;
+            if (eval_df(u, a.q, a.T, phi, band) && phi.hi + band >= lower && fabs(eval64(u, a.q, a.T) - dv) <= tol)
+                ci = min(ci, t * m + s);
         }
     }
     ci = min(red_min_i(ci, sm), di);
@@ -557,7 +578,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
         a.t_out[2 * k + 1] = s;
         if (a.t_bin) a.t_bin[k] = t;
         a.phi_out[k] = (float)dv;
-        a.status[k] = TSALLIS_OK | (nband > 1 ? TSALLIS_STATUS_RERANKED : 0);
+        a.status[k] = TSALLIS_OK | TSALLIS_STATUS_RERANKED;
     }
 }
 
@@ -617,7 +638,7 @@ cudaError_t hist2d_occupancy(int* blocks_per_sm) {
 
 size_t search2d_scratch_bytes(int L2, long long K) {
     const size_t cells = (size_t)K * L2 * L2;
-    return cells * (2 * sizeof(int) + 2 * sizeof(float2)) + (size_t)K * L2 * 4 * sizeof(float) + 256;
+    return cells * (2 * sizeof(int) + 2 * sizeof(float2)) + (size_t)K * L2 * 5 * sizeof(float) + 256;
 }
 
 cudaError_t launch_search2d(const Search2dLaunch& p, cudaStream_t s) {
@@ -634,17 +655,18 @@ cudaError_t launch_search2d(const Search2dLaunch& p, cudaStream_t s) {
     a.PC = reinterpret_cast<int*>(a.SW + cells);
     a.SC = a.PC + cells;
     float* rows = reinterpret_cast<float*>(a.SC + cells);
-    a.rphi = rows;
-    a.rerr = rows + (size_t)p.K * L2;
-    a.rupper = rows + 2 * (size_t)p.K * L2;
-    a.rs = reinterpret_cast<int*>(rows + 3 * (size_t)p.K * L2);
+    a.rvh = rows;
+    a.rvl = rows + (size_t)p.K * L2;
+    a.rband = rows + 2 * (size_t)p.K * L2;
+    a.ru2 = rows + 3 * (size_t)p.K * L2;
+    a.ri = reinterpret_cast<int*>(rows + 4 * (size_t)p.K * L2);
     a.curve = p.curve;
     a.t_out = p.t;
     a.t_bin = p.t_bin;
     a.phi_out = p.phi;
     a.status = p.status;
     k_s2_rows<<<dim3(L2, (unsigned)p.K), kS2Threads, 0, s>>>(a);
-    k_s2_cols<<<dim3((L2 + 31) / 32, (unsigned)p.K), 256, 0, s>>>(a);
+    k_s2_cols<<<dim3((L2 + 31) / 32, (unsigned)p.K), 1024, 0, s>>>(a);
     k_s2_eval<<<dim3(L2 - 1, (unsigned)p.K), kS2Threads, 0, s>>>(a);
     k_s2_final<<<(unsigned)p.K, kS2Threads, 0, s>>>(a);
     return cudaGetLastError();

@@ -24,7 +24,9 @@ __device__ __forceinline__ bool df_gt(F2 a, F2 b) { return a.hi > b.hi || (a.hi 
 // Running top of (value, level) pairs: the largest value (smallest level on
 // equal values), its error bound, and the largest value + bound among all
 // other pairs seen (u2), which decides whether anything else can still beat
-// the top.
+// the top. A pair whose value equals the top's exactly (a threshold on a
+// plateau of empty levels gives the very same sums, hence the same value)
+// does not raise u2: the smallest index already settles that tie.
 struct Top {
     F2 v;
     int i;       // level, -1: none
@@ -38,7 +40,8 @@ __device__ __forceinline__ Top top_merge(Top a, Top b) {
     const bool a_wins = df_gt(a.v, b.v) || (!df_gt(b.v, a.v) && a.i < b.i);
     Top w = a_wins ? a : b;
     const Top l = a_wins ? b : a;
-    w.u2 = fmaxf(fmaxf(w.u2, l.u2), l.v.hi + l.band);
+    const bool same = l.v.hi == w.v.hi && l.v.lo == w.v.lo;
+    w.u2 = fmaxf(fmaxf(w.u2, l.u2), same ? -INFINITY : l.v.hi + l.band);
     return w;
 }
 
