@@ -38,7 +38,6 @@ __device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
     return {hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
 }
 
-__device__ __forceinline__ F2 f2_add_f(F2 x, float y) { return f2_add(x, F2{y, 0.f}); }
 __device__ __forceinline__ float f2_val(F2 x) { return __fadd_rn(x.hi, x.lo); }
 
 __device__ __forceinline__ F2 shfl_up_f2(F2 v, int d) {
@@ -73,23 +72,6 @@ __device__ __forceinline__ F2 warp_suffix_f2(F2 v, int lane) {
     }
     return v;
 }
-__device__ __forceinline__ double warp_prefix_f64(double v, int lane) {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        double o = __shfl_up_sync(0xffffffffu, v, d);
-        if (lane >= d) v += o;
-    }
-    return v;
-}
-__device__ __forceinline__ double warp_suffix_f64(double v, int lane) {
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        double o = __shfl_down_sync(0xffffffffu, v, d);
-        if (lane + d < 32) v += o;
-    }
-    return v;
-}
-
 // (value, index) maximum; equal values keep the smaller index.
 template <typename T>
 __device__ __forceinline__ void argmax_merge(T& v, int& i, T ov, int oi) {
@@ -136,16 +118,12 @@ struct SearchSmem {
     long long cnt_pre[kSearchWarps];
     F2 w_pre[kSearchWarps];
     F2 w_suf[kSearchWarps];
-    double d_pre[kSearchWarps];
-    double d_suf[kSearchWarps];
     float red_v[kSearchWarps];
     int red_i[kSearchWarps];
     double red_dv[kSearchWarps];
     long long total;
-    float best_phi, best_err;
-    int best_t;
-    long long best_na;
-    int canon_t;
+    float best_err;
+    int nlevels;        // non-empty levels (compaction)
     int flag;
     // per-warp running tops of the table search
     float top_vh[kSearchWarps], top_vl[kSearchWarps], top_band[kSearchWarps], top_u2[kSearchWarps];
@@ -161,28 +139,6 @@ struct SearchResult {
 
 // ------------------------------------------------------------ streaming tiles
 
-__device__ __forceinline__ int level_of(int v, int lo, int L) {
-    int b = v - lo;
-    b = b < 0 ? 0 : b;
-    return b > L - 1 ? L - 1 : b;
-}
-
-__device__ __forceinline__ uint4 ld_stream_keep(const void* p) {
-    // read-only path, no L1 allocation; the line stays in L2 for the re-read
-    uint4 r;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p));
-    return r;
-}
-__device__ __forceinline__ uint4 ld_last_use(const void* p) {
-    // last use of the line: evict-first in L2
-    uint4 r;
-    asm volatile("ld.global.cs.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p));
-    return r;
-}
 __device__ __forceinline__ void st_stream(void* p, uint2 v) {
     asm volatile("st.global.cs.v2.u32 [%0], {%1,%2};" ::"l"(p), "r"(v.x), "r"(v.y) : "memory");
 }
@@ -191,15 +147,6 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
-}
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 }  // namespace tsl

@@ -87,21 +87,6 @@ __device__ __forceinline__ void block_argmax_d(double v, int i, SearchSmem& sm) 
     }
     Sync::sync();
 }
-template <class Sync>
-__device__ __forceinline__ int block_min_i(int v, SearchSmem& sm) {
-    const int lane = Sync::tid() & 31, warp = Sync::tid() >> 5;
-    v = __reduce_min_sync(0xffffffffu, v);
-    if (lane == 0) sm.red_i[warp] = v;
-    Sync::sync();
-    if (warp == 0) {
-        v = lane < kSearchWarps ? sm.red_i[lane] : 0x7fffffff;
-        v = __reduce_min_sync(0xffffffffu, v);
-        if (lane == 0) sm.canon_t = v;
-    }
-    Sync::sync();
-    return sm.canon_t;
-}
-
 // Scratch (shared memory): sT[kMaxBins] float2 and sIC[kMaxBins] int2.
 //
 // Only non-empty levels matter: every threshold t in a run of empty levels
@@ -155,7 +140,7 @@ __device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, flo
             for (int d = 16; d > 0; d >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, d);
             __syncwarp();
             if (lane < kSearchWarps) sm.red_i[lane] = vi - v;   // exclusive warp offsets
-            if (lane == kSearchWarps - 1) sm.canon_t = vi;       // M
+            if (lane == kSearchWarps - 1) sm.nlevels = vi;       // M
             if (lane == 0) sm.total = cs;
         }
         Sync::sync();
@@ -165,7 +150,7 @@ __device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, flo
             if (hv[k] > 0) sIC[pos++] = make_int2(base + k, hv[k]);
     }
     Sync::sync();
-    const int M = sm.canon_t;
+    const int M = sm.nlevels;
     const long long N = sm.total;
     if (curve != nullptr) {
         // empty class 1 below the first non-empty level
