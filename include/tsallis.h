@@ -283,6 +283,23 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* ctx, const tsallis_volume* h_v
  *   the stream.
  */
 #define TSALLIS_PROPOSER_PARAMS 1184256
+/*
+ * Training checkpoints: tsallis_proposer_checkpoint_save writes the FP32
+ * parameters, both Adam moments and the number of Adam steps taken, with a
+ * header (magic "TSCKPT01", version 1, the layer sizes) and, after the
+ * moments, user_bytes bytes of the caller's own state (for example its data
+ * sampler's random state), closed by a CRC-32 of everything before it.
+ * tsallis_proposer_checkpoint_load restores parameters, moments and step
+ * count (training then continues exactly as if uninterrupted, given the same
+ * batches) and copies the caller's state into user (at most user_cap bytes;
+ * *user_bytes receives its length). A damaged, truncated or foreign file, or
+ * a user state longer than user_cap, gives TSALLIS_ERR_INVALID_ARG and leaves
+ * the context unchanged. Both are synchronous.
+ */
+tsallis_status tsallis_proposer_checkpoint_save(tsallis_ctx* ctx, const char* path, const void* user,
+                                                int64_t user_bytes);
+tsallis_status tsallis_proposer_checkpoint_load(tsallis_ctx* ctx, const char* path, void* user, int64_t user_cap,
+                                                int64_t* user_bytes);
 tsallis_status tsallis_proposer_set(tsallis_ctx* ctx, const float* h_params, int64_t n);
 tsallis_status tsallis_proposer_get(tsallis_ctx* ctx, float* h_params, int64_t n);
 tsallis_status tsallis_proposer_load(tsallis_ctx* ctx, const char* path);

@@ -95,6 +95,9 @@ _SIGS = {
     "tsallis_proposer_load": ([_P, ctypes.c_char_p], ctypes.c_int),
     "tsallis_proposer_save": ([_P, ctypes.c_char_p], ctypes.c_int),
     "tsallis_proposer_features": ([_P, _P, _I64, _P, _P], ctypes.c_int),
+    "tsallis_proposer_checkpoint_save": ([_P, ctypes.c_char_p, _P, _I64], ctypes.c_int),
+    "tsallis_proposer_checkpoint_load": ([_P, ctypes.c_char_p, _P, _I64, ctypes.POINTER(ctypes.c_int64)],
+                                         ctypes.c_int),
     "tsallis_proposer_forward": ([_P, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
     "tsallis_proposer_train_step": ([_P, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32, _P, _P, _P],
                                     ctypes.c_int),
@@ -155,7 +158,7 @@ def set_wait_timeout(ns: int, device=None) -> None:
     _check("tsallis_set_wait_timeout", lib().tsallis_set_wait_timeout(context(device), int(ns)))
 
 
-def set_launch_shape(tile_vox: int = 32768, blocks_per_sm: int = 0, device=None) -> None:
+def set_launch_shape(tile_vox: int = 65536, blocks_per_sm: int = 0, device=None) -> None:
     """Launch shape of the persistent kernels (see tsallis_set_launch_shape)."""
     _check("tsallis_set_launch_shape",
            lib().tsallis_set_launch_shape(context(device), int(tile_vox), int(blocks_per_sm)))
@@ -407,3 +410,19 @@ def proposer_train_step(x: torch.Tensor, y: torch.Tensor, lr: float = 1e-3, upda
         context(x.device), x.data_ptr(), y.data_ptr(), x.shape[0], float(lr), 1 if update else 0, loss.data_ptr(),
         g.data_ptr() if g is not None else None, _stream(x)))
     return loss, g
+
+
+def proposer_checkpoint_save(path: str, user: bytes = b"", device=None) -> None:
+    """Parameters, Adam state and step count, plus the caller's own bytes."""
+    buf = ctypes.create_string_buffer(user, len(user)) if user else None
+    _check("tsallis_proposer_checkpoint_save", lib().tsallis_proposer_checkpoint_save(
+        context(device), os.fsencode(path), buf, len(user)))
+
+
+def proposer_checkpoint_load(path: str, user_cap: int = 1 << 20, device=None) -> bytes:
+    """Restores a checkpoint; returns the caller's bytes saved with it."""
+    buf = ctypes.create_string_buffer(max(user_cap, 1))
+    n = ctypes.c_int64(0)
+    _check("tsallis_proposer_checkpoint_load", lib().tsallis_proposer_checkpoint_load(
+        context(device), os.fsencode(path), buf, user_cap, ctypes.byref(n)))
+    return buf.raw[: n.value]

@@ -1057,6 +1057,107 @@ tsallis_status tsallis_proposer_save(tsallis_ctx* c, const char* path) {
     return (std::fclose(f) == 0 && ok) ? TSALLIS_OK : TSALLIS_ERR_INVALID_ARG;
 }
 
+namespace {
+// CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320), bytewise from the
+// definition: shift out one bit at a time, folding in the polynomial when
+// the bit shifted out is set.
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+    const unsigned char* p = static_cast<const unsigned char*>(data);
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) {
+        crc ^= p[i];
+        for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+    }
+    return ~crc;
+}
+
+const char kCkptMagic[8] = {'T', 'S', 'C', 'K', 'P', 'T', '0', '1'};
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;   // 1
+    uint32_t nin, nhid, nout;
+    uint32_t pad;
+    int64_t nparams;
+    int64_t step;       // Adam steps taken
+    int64_t user_bytes; // caller's state that follows the moments
+};
+}  // namespace
+
+tsallis_status tsallis_proposer_checkpoint_save(tsallis_ctx* c, const char* path, const void* user,
+                                                int64_t user_bytes) {
+    if (!c || !path || !c->mlp_ready || user_bytes < 0 || (user_bytes > 0 && !user)) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    const size_t f = (size_t)kMlpParams * sizeof(float);
+    std::vector<float> buf(3 * (size_t)kMlpParams);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(buf.data(), c->mlp.p32, f, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(buf.data() + kMlpParams, c->mlp.m, f, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(buf.data() + 2 * kMlpParams, c->mlp.v, f, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TSALLIS_ERR_CUDA;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.nin = kMlpIn;
+    h.nhid = kMlpHid;
+    h.nout = kMlpOut;
+    h.nparams = kMlpParams;
+    h.step = c->mlp_step;
+    h.user_bytes = user_bytes;
+    uint32_t crc = crc32_update(0, &h, sizeof(h));
+    crc = crc32_update(crc, buf.data(), buf.size() * sizeof(float));
+    if (user_bytes > 0) crc = crc32_update(crc, user, (size_t)user_bytes);
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return TSALLIS_ERR_INVALID_ARG;
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 &&
+              std::fwrite(buf.data(), sizeof(float), buf.size(), fp) == buf.size() &&
+              (user_bytes == 0 || std::fwrite(user, 1, (size_t)user_bytes, fp) == (size_t)user_bytes) &&
+              std::fwrite(&crc, sizeof(crc), 1, fp) == 1;
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? TSALLIS_OK : TSALLIS_ERR_INVALID_ARG;
+}
+
+tsallis_status tsallis_proposer_checkpoint_load(tsallis_ctx* c, const char* path, void* user, int64_t user_cap,
+                                                int64_t* user_bytes) {
+    if (!c || !path || user_cap < 0 || (user_cap > 0 && !user)) return TSALLIS_ERR_INVALID_ARG;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return TSALLIS_ERR_INVALID_ARG;
+    CkptHeader h;
+    std::vector<float> buf;
+    std::vector<unsigned char> ub;
+    uint32_t crc_file = 0;
+    bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::memcmp(h.magic, kCkptMagic, 8) == 0 && h.version == 1 &&
+              h.nin == (uint32_t)kMlpIn && h.nhid == (uint32_t)kMlpHid && h.nout == (uint32_t)kMlpOut &&
+              h.nparams == kMlpParams && h.step >= 0 && h.user_bytes >= 0 && h.user_bytes <= (1ll << 30);
+    if (ok) {
+        buf.resize(3 * (size_t)kMlpParams);
+        ub.resize((size_t)h.user_bytes);
+        ok = std::fread(buf.data(), sizeof(float), buf.size(), fp) == buf.size() &&
+             (h.user_bytes == 0 || std::fread(ub.data(), 1, ub.size(), fp) == ub.size()) &&
+             std::fread(&crc_file, sizeof(crc_file), 1, fp) == 1;
+    }
+    std::fclose(fp);
+    if (!ok) return TSALLIS_ERR_INVALID_ARG;
+    uint32_t crc = crc32_update(0, &h, sizeof(h));
+    crc = crc32_update(crc, buf.data(), buf.size() * sizeof(float));
+    if (!ub.empty()) crc = crc32_update(crc, ub.data(), ub.size());
+    if (crc != crc_file) return TSALLIS_ERR_INVALID_ARG;   // damaged file
+    if (h.user_bytes > user_cap) return TSALLIS_ERR_INVALID_ARG;
+    tsallis_status st = tsallis_proposer_set(c, buf.data(), kMlpParams);
+    if (st != TSALLIS_OK) return st;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    const size_t f = (size_t)kMlpParams * sizeof(float);
+    if (cudaMemcpy(c->mlp.m, buf.data() + kMlpParams, f, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->mlp.v, buf.data() + 2 * kMlpParams, f, cudaMemcpyHostToDevice) != cudaSuccess)
+        return TSALLIS_ERR_CUDA;
+    c->mlp_step = (int)h.step;
+    if (!ub.empty()) std::memcpy(user, ub.data(), ub.size());
+    if (user_bytes) *user_bytes = h.user_bytes;
+    return TSALLIS_OK;
+}
+
 tsallis_status tsallis_proposer_features(tsallis_ctx* c, const int32_t* d_hist, int64_t nh, float* d_x,
                                          cudaStream_t stream) {
     if (!c || nh < 0 || (nh > 0 && (!d_hist || !d_x))) return TSALLIS_ERR_INVALID_ARG;

@@ -11,7 +11,9 @@ the labelled partition (the labelled level and the empty levels after it).
 
 Training: Adam on the mean soft-target cross-entropy (the library's
 forward, backward and optimiser kernels), minibatches drawn with a seeded
-generator. The result is written with tsallis_proposer_save.
+generator. The result is written with tsallis_proposer_save. With
+--checkpoint the training state is saved every --checkpoint-every steps and
+--resume continues an interrupted run exactly.
 
     python -m paper_2012_10684_gb300.proposer --out weights.bin
 """
@@ -69,22 +71,43 @@ def make_dataset(n: int, seed: int, dmin: int, dmax: int, q: float = 0.8, nx: in
     return hist, sub, t, st
 
 
+def _pack_state(s: int, gen: torch.Generator) -> bytes:
+    """The trainer's own state stored in a checkpoint: the next step number
+    and the minibatch generator's state."""
+    return int(s).to_bytes(8, "little") + gen.get_state().cpu().numpy().tobytes()
+
+
 def train(x: torch.Tensor, y: torch.Tensor, steps: int, batch: int, lr: float, seed: int, init_seed: int = 1,
-          log_every: int = 0):
+          log_every: int = 0, checkpoint: str | None = None, checkpoint_every: int = 0, resume: str | None = None,
+          stop_after: int | None = None):
     """Trains the context's proposer from a seeded initialisation; returns
-    the loss of every step."""
-    g = np.random.default_rng(init_seed)
-    params = []
-    for fan_out, fan_in in ((256, 256), (256, 256), (4096, 256)):
-        bound = math.sqrt(6.0 / (fan_in + fan_out))
-        params.append(g.uniform(-bound, bound, fan_out * fan_in))
-        params.append(np.zeros(fan_out))
-    tg.proposer_set(np.concatenate(params).astype(np.float32), x.device)
+    the loss of every step taken (NaN for the steps a resumed run skipped).
+
+    With checkpoint and checkpoint_every, the parameters, Adam moments and
+    step count (tsallis_proposer_checkpoint_save) and the minibatch
+    generator's state are written every checkpoint_every steps; resume
+    restores them and continues, so that a resumed run ends with the same
+    parameters, bit for bit, as one that was never interrupted. stop_after
+    ends the run after that many steps (an interrupted run)."""
     gen = torch.Generator(device=x.device)
     gen.manual_seed(seed)
-    losses = torch.empty(steps, dtype=torch.float32, device=x.device)
+    start = 0
+    if resume:
+        user = tg.proposer_checkpoint_load(resume, device=x.device)
+        start = int.from_bytes(user[:8], "little")
+        gen.set_state(torch.frombuffer(bytearray(user[8:]), dtype=torch.uint8))
+    else:
+        g = np.random.default_rng(init_seed)
+        params = []
+        for fan_out, fan_in in ((256, 256), (256, 256), (4096, 256)):
+            bound = math.sqrt(6.0 / (fan_in + fan_out))
+            params.append(g.uniform(-bound, bound, fan_out * fan_in))
+            params.append(np.zeros(fan_out))
+        tg.proposer_set(np.concatenate(params).astype(np.float32), x.device)
+    losses = torch.full((steps,), float("nan"), dtype=torch.float32, device=x.device)
     n = x.shape[0]
-    for s in range(steps):
+    end = steps if stop_after is None else min(steps, stop_after)
+    for s in range(start, end):
         # cosine decay of the learning rate
         lr_s = lr * 0.5 * (1 + math.cos(math.pi * s / steps))
         idx = torch.randint(0, n, (batch,), device=x.device, generator=gen)
@@ -92,6 +115,8 @@ def train(x: torch.Tensor, y: torch.Tensor, steps: int, batch: int, lr: float, s
         losses[s] = loss[0]
         if log_every and (s + 1) % log_every == 0:
             print("step %d loss %.4f" % (s + 1, float(losses[s])), flush=True)
+        if checkpoint and checkpoint_every and (s + 1) % checkpoint_every == 0:
+            tg.proposer_checkpoint_save(checkpoint, _pack_state(s + 1, gen), device=x.device)
     return losses.cpu().numpy()
 
 
@@ -105,6 +130,9 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=2012106845)
     ap.add_argument("--out", required=True)
+    ap.add_argument("--checkpoint", help="training checkpoint written every --checkpoint-every steps")
+    ap.add_argument("--checkpoint-every", type=int, default=1000)
+    ap.add_argument("--resume", help="checkpoint to continue from (same data arguments)")
     args = ap.parse_args()
     import __graft_entry__
     __graft_entry__.build()
@@ -119,10 +147,12 @@ def main():
     y = torch.cat([y, y])
     torch.cuda.synchronize()
     t1 = time.time()
-    losses = train(x, y, args.steps, args.batch, args.lr, args.seed, log_every=500)
+    losses = train(x, y, args.steps, args.batch, args.lr, args.seed, log_every=500, checkpoint=args.checkpoint,
+                   checkpoint_every=args.checkpoint_every, resume=args.resume)
     torch.cuda.synchronize()
     tg.proposer_save(args.out)
-    print("data %.1f s, training %.1f s, final loss %.4f" % (t1 - t0, time.time() - t1, losses[-100:].mean()))
+    print("data %.1f s, training %.1f s, final loss %.4f" % (t1 - t0, time.time() - t1,
+                                                             np.nanmean(losses[-100:])))
 
 
 if __name__ == "__main__":

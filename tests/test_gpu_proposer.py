@@ -126,6 +126,36 @@ def test_save_load_round_trip(tmp_path):
     assert np.array_equal(tg.proposer_get(), params)
 
 
+def test_checkpoint_resume_is_bit_exact(tmp_path):
+    """An interrupted run (stopped after 7 of 20 steps, checkpoint every 7)
+    resumed from its checkpoint ends with the same parameters, bit for bit,
+    as the uninterrupted run; a damaged checkpoint is refused and leaves the
+    context as it was. (The loss is summed over rows with atomics, so only
+    its value, not its last bits, is compared.)"""
+    rng = np.random.default_rng(14)
+    h = torch.from_numpy(_histograms(15, 64)).cuda()
+    t = torch.tensor([int(np.flatnonzero(r)[len(np.flatnonzero(r)) // 3]) for r in h.cpu().numpy()],
+                     dtype=torch.int32, device="cuda")
+    x, y = tg.proposer_features(h), P.soft_targets(h, t)
+    kw = dict(steps=20, batch=16, lr=2e-3, seed=int(rng.integers(1 << 30)))
+    full = P.train(x, y, **kw)
+    p_full = tg.proposer_get()
+    ck = str(tmp_path / "c.ckpt")
+    part = P.train(x, y, checkpoint=ck, checkpoint_every=7, stop_after=8, **kw)
+    assert np.isnan(part[8:]).all() and np.allclose(part[:8], full[:8], rtol=1e-5)
+    tg.proposer_set(_params(16))                     # another run's weights in between
+    rest = P.train(x, y, resume=ck, **kw)
+    assert np.isnan(rest[:7]).all() and np.allclose(rest[7:], full[7:], rtol=1e-5)
+    assert np.array_equal(tg.proposer_get(), p_full)
+    raw = bytearray(open(ck, "rb").read())
+    raw[100] ^= 1
+    bad = str(tmp_path / "bad.ckpt")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(RuntimeError):
+        tg.proposer_checkpoint_load(bad)
+    assert np.array_equal(tg.proposer_get(), p_full)
+
+
 def test_training_reduces_the_loss():
     v = torch.from_numpy(phantom.generate_host(phantom.chest_volume(43, nz=64))).cuda()
     p = tg.tsallis_params(q=0.8, mode="slice")
