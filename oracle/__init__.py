@@ -40,6 +40,8 @@ _SIGS = {
     "oracle_argmax2d": [P, P, P, I32, P, P, P, P],
     "oracle_binarize": [P, I64, I32, I32, I32, I32, I32, P],
     "oracle_segment1d": [P, I64, I64, I32, I32, F64, I32, I32, I32, P, P, P, P],
+    "oracle_rescale8": [P, I64, I32, I32, I32, P],
+    "oracle_morph2d": [P, I64, I64, I64, I32, I32, P],
 }
 
 
@@ -196,3 +198,38 @@ def segment1d(vol, group_voxels: int, q: float, lo: int = -1024, L: int = 4096, 
     _check(lib().oracle_segment1d(_ptr(v), group_voxels, ng, lo, L, float(q), polarity, int(definition), nthreads,
                                   _ptr(t), _ptr(phi), _ptr(gap), _ptr(mask)), "segment1d")
     return t, phi, gap, mask
+
+
+MORPH_OPS = {"copy": 0, "erode": 1, "dilate": 2, "open": 3, "close": 4, "chest_mask": 5, "black_tophat": 6}
+
+
+def rescale8(vol, background: int = -2000, hu_min: int = -2000, hu_max: int = 2500) -> np.ndarray:
+    """Section II-B pre-processing: CT numbers to 8-bit grey levels."""
+    v = np.ascontiguousarray(vol, np.int16)
+    g = np.empty(v.shape, np.uint8)
+    _check(lib().oracle_rescale8(_ptr(v), v.size, background, hu_min, hu_max, _ptr(g)), "rescale8")
+    return g
+
+
+def morph2d(img, r: int = 10, op: str = "chest_mask") -> np.ndarray:
+    """Section II-C morphology on each slice of a uint8 [nz][ny][nx] image
+    with the disk of radius r."""
+    a = np.ascontiguousarray(img, np.uint8)
+    a3 = a.reshape((-1,) + a.shape[-2:])
+    o = np.empty(a3.shape, np.uint8)
+    _check(lib().oracle_morph2d(_ptr(a3), a3.shape[2], a3.shape[1], a3.shape[0], r, MORPH_OPS[op], _ptr(o)),
+           "morph2d")
+    return o.reshape(a.shape)
+
+
+def preprocess(vol, r: int = 10, op: str = "chest_mask", background: int = -2000, hu_min: int = -2000,
+               hu_max: int = 2500, per_slice: bool = True):
+    """Pre-processing and morphology of a [nz][ny][nx] CT volume: the 8-bit
+    image after the chest-mask step (as int16 levels 0..255) and its 256-level
+    histograms, one per slice (per_slice) or one for the volume."""
+    g = rescale8(vol, background, hu_min, hu_max)
+    o = morph2d(g, r, op).astype(np.int16)
+    o3 = o.reshape((-1,) + o.shape[-2:])
+    groups = o3.reshape(o3.shape[0], -1) if per_slice else o3.reshape(1, -1)
+    h = np.stack([hist1d(gr, lo=0, L=256) for gr in groups]).astype(np.int64)
+    return o, h

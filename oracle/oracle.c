@@ -480,3 +480,91 @@ int oracle_segment1d(const int16_t* vol, int64_t nvox_group, int64_t ngroups, in
     free(th);
     return rc;
 }
+
+/* ------------------------------------------------------------ pre-processing */
+
+/*
+ * Section II-B "Pre-processing": the CT numbers are turned into an 8-bit
+ * grey image. Readings (the text gives no formula): a voxel at or below the
+ * detector background value (-2000 HU) becomes 0; every other value is
+ * clamped to [hu_min, hu_max] (by default the histogram range of Fig. 3,
+ * -2000..2500) and mapped linearly onto 0..255, rounded to the nearest level
+ * with halves rounded up: g = floor((v - hu_min) * 255 / (hu_max - hu_min) + 1/2),
+ * computed here in exact integer arithmetic.
+ */
+int oracle_rescale8(const int16_t* vol, int64_t n, int32_t background, int32_t hu_min, int32_t hu_max,
+                    uint8_t* out) {
+    if (!vol || !out || n < 0 || hu_max <= hu_min) return 1;
+    const int64_t D = (int64_t)hu_max - hu_min;
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t v = vol[k];
+        if (v <= background) { out[k] = 0; continue; }
+        if (v < hu_min) v = hu_min;
+        if (v > hu_max) v = hu_max;
+        /* (v - hu_min) * 255 / D + 1/2, floored: numerator and denominator doubled */
+        int64_t g = (2 * (v - hu_min) * 255 + D) / (2 * D);
+        out[k] = (uint8_t)g;
+    }
+    return 0;
+}
+
+/*
+ * Section II-C "Morphology": erosion and dilation of the grey image A by a
+ * flat structuring element B, opening (erosion, then dilation), and the
+ * chest-mask subtraction. B is the digital disk of radius r: the offsets
+ * (dx, dy) with dx^2 + dy^2 <= r^2 (r = 10 reads the paper's disk of size 10
+ * pixels). Flat grey erosion is the minimum of A over B placed at the pixel,
+ * dilation the maximum (B is symmetric, so B and its reflection agree).
+ * Offsets that leave the image are not part of the window. Each slice (z) is
+ * a separate 2-D image, as in the paper.
+ *
+ * op: 1 erosion, 2 dilation, 3 opening, 4 closing (dilation, then erosion),
+ * 5 chest-mask subtraction A - opening(A), 6 closing(A) - A. The text
+ * subtracts the image from its opening; an opening never exceeds the image,
+ * so that difference is read with the sign that leaves it non-negative
+ * (op 5). op 0 copies A.
+ */
+static void morph_pass(const uint8_t* in, int64_t nx, int64_t ny, int32_t r, int use_max, uint8_t* out) {
+    for (int64_t y = 0; y < ny; ++y)
+        for (int64_t x = 0; x < nx; ++x) {
+            int v = use_max ? 0 : 255;
+            for (int32_t dy = -r; dy <= r; ++dy)
+                for (int32_t dx = -r; dx <= r; ++dx) {
+                    if (dx * dx + dy * dy > r * r) continue;
+                    int64_t xx = x + dx, yy = y + dy;
+                    if (xx < 0 || xx >= nx || yy < 0 || yy >= ny) continue;
+                    int a = in[yy * nx + xx];
+                    if (use_max ? a > v : a < v) v = a;
+                }
+            out[y * nx + x] = (uint8_t)v;
+        }
+}
+
+int oracle_morph2d(const uint8_t* img, int64_t nx, int64_t ny, int64_t nz, int32_t r, int32_t op, uint8_t* out) {
+    if (!img || !out || nx < 1 || ny < 1 || nz < 0 || r < 0 || op < 0 || op > 6) return 1;
+    const int64_t ns = nx * ny;
+    uint8_t* a = (uint8_t*)malloc((size_t)ns);
+    uint8_t* b = (uint8_t*)malloc((size_t)ns);
+    if (!a || !b) { free(a); free(b); return 2; }
+    for (int64_t z = 0; z < nz; ++z) {
+        const uint8_t* A = img + z * ns;
+        uint8_t* O = out + z * ns;
+        switch (op) {
+            case 0: memcpy(O, A, (size_t)ns); break;
+            case 1: morph_pass(A, nx, ny, r, 0, O); break;
+            case 2: morph_pass(A, nx, ny, r, 1, O); break;
+            case 3: morph_pass(A, nx, ny, r, 0, a); morph_pass(a, nx, ny, r, 1, O); break;
+            case 4: morph_pass(A, nx, ny, r, 1, a); morph_pass(a, nx, ny, r, 0, O); break;
+            case 5:
+                morph_pass(A, nx, ny, r, 0, a); morph_pass(a, nx, ny, r, 1, b);
+                for (int64_t k = 0; k < ns; ++k) O[k] = (uint8_t)(A[k] - b[k]);
+                break;
+            case 6:
+                morph_pass(A, nx, ny, r, 1, a); morph_pass(a, nx, ny, r, 0, b);
+                for (int64_t k = 0; k < ns; ++k) O[k] = (uint8_t)(b[k] - A[k]);
+                break;
+        }
+    }
+    free(a); free(b);
+    return 0;
+}
