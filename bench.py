@@ -352,6 +352,80 @@ def two_d_leg(dev, steps=10, warmup=3):
                          "bytes_per_voxel": 5}}
 
 
+def preprocess_leg(dev, steps=10, warmup=3, nz=NZ):
+    """The steps before the threshold (8-bit levels, chest-mask opening with
+    the disk of radius 10 and subtraction, 256-level slice histograms) in
+    one launch, and the paper's whole segmentation step (that launch, the
+    per-slice Tsallis search on 256 levels, Algorithm 1) on the 512x512x400
+    chest phantom. Algorithmic bytes of the fused kernel: 4 per voxel (read
+    the CT number, write the level); of the whole step: 7 (plus the
+    binarise pass: read the level, write the mask)."""
+    import torch
+
+    import phantom
+    import paper_2012_10684_gb300 as tg
+    vol = phantom.generate_cuda(phantom.chest_volume(2012106842, NX, NY, nz), device=dev)
+    pp = tg.preprocess_params()
+    lev = torch.empty(vol.shape, dtype=torch.int16, device=dev)
+    hist = torch.empty((nz, 256), dtype=torch.int32, device=dev)
+    mask = torch.empty(vol.shape, dtype=torch.uint8, device=dev)
+    p = tg.tsallis_params(q=Q, lo=0, nbins=256, mode="slice")
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    ms_pre = timed(lambda: tg.tsallis_preprocess(vol, pp, out=lev, hist=hist))
+    res = {}
+
+    def step():
+        tg.tsallis_preprocess(vol, pp, out=lev, hist=hist)
+        t, _, st = tg.tsallis_search(hist, p)
+        tg.tsallis_binarize(lev, t, p, out=mask)
+        res["st"] = st
+    ms_step = timed(step)
+    assert int((res["st"] & 0xff).max().item()) == 0
+    peak, _ = _peaks()
+    n = vol.numel()
+    achieved = 4 * n / (ms_pre / 1e3) / 1e9
+    # ALU roofline: the chord method needs, per pixel and pass, 2R extremes
+    # for the chords of half-width 1..R and 2R to fold the 2R+1 chords of the
+    # disk: 4R scalar min/max, 2R fp16x2 instructions; two passes (opening).
+    # Peak: 64 ALU lanes per clock per SM x SMs x maximum SM clock.
+    r = pp.radius
+    alu_ops = 2 * 2 * r * n
+    props = torch.cuda.get_device_properties(dev)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+        src = "sm_max_mhz of MEASURED_PEAKS.json"
+    except (OSError, KeyError, ValueError):
+        mhz, src = 2070.0, "nominal max SM clock"
+    alu_peak = 64 * props.multi_processor_count * mhz * 1e6 / 1e9
+    alu_ach = alu_ops / (ms_pre / 1e3) / 1e9
+    return {"workload": "chest phantom 512x512x%d: 8-bit levels, chest-mask opening (disk radius 10), "
+                        "slice histograms; then per-slice Tsallis q=0.8 on 256 levels and Algorithm 1" % nz,
+            "preprocess": {"value": n / (ms_pre / 1e3), "unit": "voxels/s", "ms": ms_pre,
+                           "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
+                                        "unit": "G fp16x2 min/max per s", "frac": alu_ach / alu_peak,
+                                        "ops_per_voxel": 4 * r, "peak_basis": "64 lanes/clk/SM, " + src},
+                           "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                   "bytes_per_voxel": 4}},
+            "segmentation_step": {"value": n / (ms_step / 1e3), "unit": "voxels/s", "ms": ms_step,
+                                  "launches": 3},
+            "steps": steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,6 +438,9 @@ def main():
                     help="run only the batch leg (for profiling; prints the leg's JSON object)")
     ap.add_argument("--batch-nvol", type=int, default=64)
     ap.add_argument("--batch-dmax", type=int, default=600)
+    ap.add_argument("--preprocess-only", action="store_true",
+                    help="print only the pre-processing / chest-mask leg (for profiling)")
+    ap.add_argument("--preprocess-nz", type=int, default=NZ, help="slices of the pre-processing leg's volume")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -389,6 +466,10 @@ def main():
     import __graft_entry__
     if rank == 0 or world == 1:
         __graft_entry__.build()
+    if args.preprocess_only:
+        torch.cuda.set_device(local)
+        print(json.dumps(preprocess_leg(torch.device("cuda", local), nz=args.preprocess_nz)), flush=True)
+        return 0
     if args.batch_only:
         torch.cuda.set_device(local)
         print(json.dumps(batch_leg(torch.device("cuda", local), nvol=args.batch_nvol, dmax=args.batch_dmax)),
@@ -491,6 +572,7 @@ def main():
     }
     if not args.no_batch:
         line["two_d"] = two_d_leg(dev)
+        line["preprocess"] = preprocess_leg(dev)
         line["batch"] = batch_leg(dev)
         line["gpu_launches_batch"] = 2 * line["batch"]["steps"]
     if not args.no_cpu_baseline and world >= 1:

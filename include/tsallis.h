@@ -357,6 +357,67 @@ tsallis_status tsallis_segment_static(const int16_t* d_vol, int64_t nx, int64_t 
                                       const tsallis_params* p, uint8_t* d_mask, int32_t* d_t, float* d_phi,
                                       int32_t* d_status, cudaStream_t stream);
 
+/*
+ * Pre-processing and chest-mask morphology: the steps of the paper that come
+ * before the threshold (section II-B "Pre-processing", section II-C
+ * "Morphology"), in one pass over the volume.
+ *
+ *   level   each CT number v becomes an 8-bit grey level: 0 when
+ *           v <= background (the detector background, -2000 HU), otherwise
+ *           v is clamped to [hu_min, hu_max] and mapped linearly onto 0..255,
+ *           rounded to nearest with halves up:
+ *           g = floor((clamp(v) - hu_min) * 255 / (hu_max - hu_min) + 1/2).
+ *   morph   flat grey morphology of each z slice as a 2-D image with the
+ *           digital disk of radius `radius` (offsets dx^2 + dy^2 <= r^2;
+ *           offsets that leave the slice are not part of the window):
+ *           erosion = minimum over the disk, dilation = maximum, opening =
+ *           dilation of the erosion, closing = erosion of the dilation.
+ *   op      the output: TSALLIS_MORPH_CHEST_MASK = g - opening(g), the
+ *           chest-mask subtraction (the paper opens with a disk of size 10
+ *           and subtracts; an opening never exceeds the image, so the
+ *           difference is taken in the order that keeps it non-negative);
+ *           TSALLIS_MORPH_BLACK_TOPHAT = closing(g) - g; or the erosion,
+ *           dilation, opening, closing, or g itself (TSALLIS_MORPH_NONE).
+ *
+ * d_vol   device int16 [nz][ny][nx] (x fastest), 4-byte aligned
+ *         (TSALLIS_ERR_ALIGNMENT otherwise).
+ * d_out   device int16 [nz][ny][nx] receiving the result as levels 0..255
+ *         (nullable); the same layout the other calls read, so that
+ *         tsallis_search / tsallis_binarize / tsallis_segment with lo = 0,
+ *         nbins = 256 threshold it. Must not overlap d_vol.
+ * d_hist  device int32, 256 counts of the result's levels per slice
+ *         ([nz][256], per_slice = 1) or for the volume ([256]); nullable;
+ *         zeroed and filled by the call.
+ * Limits: radius 0..15; hu_min < hu_max <= hu_min + 65535; nx, ny >= 1,
+ * nz >= 0, at most 2^31 - 1 tiles of 128 x 64 pixels; d_out and d_hist not both
+ * null (unless nz = 0, which writes nothing but the zeroed volume histogram).
+ * Violations return TSALLIS_ERR_INVALID_ARG before anything is enqueued.
+ * Asynchronous on `stream`; no scratch memory.
+ */
+typedef enum {
+    TSALLIS_MORPH_NONE = 0,
+    TSALLIS_MORPH_ERODE = 1,
+    TSALLIS_MORPH_DILATE = 2,
+    TSALLIS_MORPH_OPEN = 3,
+    TSALLIS_MORPH_CLOSE = 4,
+    TSALLIS_MORPH_CHEST_MASK = 5,
+    TSALLIS_MORPH_BLACK_TOPHAT = 6
+} tsallis_morph_op;
+
+typedef struct {
+    int32_t background; /* -2000 */
+    int32_t hu_min;     /* -2000 */
+    int32_t hu_max;     /* 2500 */
+    int32_t radius;     /* 10 */
+    int32_t op;         /* TSALLIS_MORPH_CHEST_MASK */
+    int32_t per_slice;  /* 1 */
+} tsallis_preprocess_params;
+
+tsallis_status tsallis_preprocess_params_default(tsallis_preprocess_params* pp);
+tsallis_status tsallis_preprocess(tsallis_ctx* ctx, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                                  const tsallis_preprocess_params* pp, int16_t* d_out, int32_t* d_hist,
+                                  cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

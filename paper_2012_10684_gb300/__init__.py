@@ -25,6 +25,7 @@ from . import build as _build
 __all__ = [
     "Params", "TsallisError", "lib", "tsallis_params", "tsallis_histogram", "tsallis_search",
     "tsallis_binarize", "tsallis_segment", "tsallis_segment_batch", "tsallis_status_string",
+    "tsallis_preprocess", "preprocess_params",
     "TSALLIS_OK", "TSALLIS_ERR_NO_VALID_THRESHOLD", "TSALLIS_ERR_TIMEOUT", "TSALLIS_STATUS_RERANKED",
 ]
 
@@ -58,6 +59,15 @@ class Volume(ctypes.Structure):
     """Mirror of ``tsallis_volume``."""
     _fields_ = [("vol", ctypes.c_void_p), ("mask", ctypes.c_void_p),
                 ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
+
+
+class PreprocessParams(ctypes.Structure):
+    """Mirror of ``tsallis_preprocess_params``."""
+    _fields_ = [("background", ctypes.c_int32), ("hu_min", ctypes.c_int32), ("hu_max", ctypes.c_int32),
+                ("radius", ctypes.c_int32), ("op", ctypes.c_int32), ("per_slice", ctypes.c_int32)]
+
+
+MORPH_OPS = {"none": 0, "erode": 1, "dilate": 2, "open": 3, "close": 4, "chest_mask": 5, "black_tophat": 6}
 
 
 class TsallisError(RuntimeError):
@@ -101,6 +111,8 @@ _SIGS = {
     "tsallis_proposer_forward": ([_P, _P, ctypes.c_int32, _P, _P], ctypes.c_int),
     "tsallis_proposer_train_step": ([_P, _P, _P, ctypes.c_int32, ctypes.c_float, ctypes.c_int32, _P, _P, _P],
                                     ctypes.c_int),
+    "tsallis_preprocess_params_default": ([ctypes.POINTER(PreprocessParams)], ctypes.c_int),
+    "tsallis_preprocess": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(PreprocessParams), _P, _P, _P], ctypes.c_int),
     "tsallis_probe_dfmath": ([_P, _P, _I64, ctypes.c_uint32, ctypes.c_float, _P, _P, _P], ctypes.c_int),
 }
 
@@ -426,3 +438,29 @@ def proposer_checkpoint_load(path: str, user_cap: int = 1 << 20, device=None) ->
     _check("tsallis_proposer_checkpoint_load", lib().tsallis_proposer_checkpoint_load(
         context(device), os.fsencode(path), buf, user_cap, ctypes.byref(n)))
     return buf.raw[: n.value]
+
+
+def preprocess_params(op="chest_mask", radius: int = 10, background: int = -2000, hu_min: int = -2000,
+                      hu_max: int = 2500, per_slice: bool = True) -> PreprocessParams:
+    pp = PreprocessParams()
+    _check("tsallis_preprocess_params_default", lib().tsallis_preprocess_params_default(ctypes.byref(pp)))
+    pp.op = MORPH_OPS[op] if isinstance(op, str) else int(op)
+    pp.radius, pp.background, pp.hu_min, pp.hu_max = int(radius), int(background), int(hu_min), int(hu_max)
+    pp.per_slice = int(bool(per_slice))
+    return pp
+
+
+def tsallis_preprocess(vol: torch.Tensor, pp: PreprocessParams | None = None, out: torch.Tensor | None = None,
+                       hist: torch.Tensor | None = None, want_out: bool = True, want_hist: bool = True):
+    """8-bit pre-processing and chest-mask morphology of a CT volume:
+    (levels int16 [nz][ny][nx] or None, int32 histograms [nh][256] or None)."""
+    pp = pp or preprocess_params()
+    nx, ny, nz = _vol3(vol)
+    if want_out and out is None:
+        out = torch.empty(vol.shape, dtype=torch.int16, device=vol.device)
+    if want_hist and hist is None:
+        hist = torch.empty((nz if pp.per_slice else 1, 256), dtype=torch.int32, device=vol.device)
+    _check("tsallis_preprocess", lib().tsallis_preprocess(
+        context(vol.device), vol.data_ptr(), nx, ny, nz, ctypes.byref(pp),
+        out.data_ptr() if want_out else None, hist.data_ptr() if want_hist else None, _stream(vol)))
+    return (out if want_out else None), (hist if want_hist else None)

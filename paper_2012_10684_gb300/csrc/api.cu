@@ -524,6 +524,11 @@ tsallis_status tsallis_create(tsallis_ctx** out, int device) {
         cudaGetLastError();
         c->cluster_max = 0;   // the tile kernel serves every shape
     }
+    if (preproc_prepare() != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return TSALLIS_ERR_CUDA;
+    }
     if (seg2d_prepare() != cudaSuccess || hist2d_occupancy(&c->hist2d_blocks_per_sm) != cudaSuccess ||
         c->hist2d_blocks_per_sm < 1) {
         cudaGetLastError();
@@ -1266,3 +1271,85 @@ tsallis_status tsallis_autotune_batch(tsallis_ctx* c, const tsallis_volume* h_vo
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ pre-processing
+
+tsallis_status tsallis_preprocess_params_default(tsallis_preprocess_params* pp) {
+    if (!pp) return TSALLIS_ERR_INVALID_ARG;
+    pp->background = -2000;
+    pp->hu_min = -2000;
+    pp->hu_max = 2500;
+    pp->radius = 10;
+    pp->op = TSALLIS_MORPH_CHEST_MASK;
+    pp->per_slice = 1;
+    return TSALLIS_OK;
+}
+
+namespace {
+// Multiplier and shift with floor(n / d) == (n * m) >> s for every n the
+// level map forms (n <= 511 * D < 2^26): m = floor(2^s / d) + 1 with
+// s = 26 + ceil(log2 d) keeps the error below 1/d; checked exhaustively.
+bool level_divider(int D, unsigned long long* m, int* s) {
+    const unsigned long long d = 2ull * (unsigned long long)D;
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    *s = 26 + l;
+    *m = ((1ull << *s) / d) + 1;
+    for (long long c = 0; c <= D; ++c) {
+        const unsigned long long n = (unsigned long long)(2 * c * 255 + D);
+        if (((n * *m) >> *s) != n / d) return false;
+    }
+    return true;
+}
+}  // namespace
+
+tsallis_status tsallis_preprocess(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                                  const tsallis_preprocess_params* pp, int16_t* d_out, int32_t* d_hist,
+                                  cudaStream_t stream) {
+    if (!c || !pp) return TSALLIS_ERR_INVALID_ARG;
+    if (pp->radius < 0 || pp->radius > kPreMaxRadius || pp->op < TSALLIS_MORPH_NONE ||
+        pp->op > TSALLIS_MORPH_BLACK_TOPHAT || (pp->per_slice != 0 && pp->per_slice != 1))
+        return TSALLIS_ERR_INVALID_ARG;
+    if ((long long)pp->hu_max - pp->hu_min < 1 || (long long)pp->hu_max - pp->hu_min > 65535)
+        return TSALLIS_ERR_INVALID_ARG;
+    if (nx < 1 || ny < 1 || nz < 0 || nx > (1 << 30) || ny > (1 << 30)) return TSALLIS_ERR_INVALID_ARG;
+    if (nz == 0 && (pp->per_slice || !d_hist)) return TSALLIS_OK;   // nothing to write
+    if (!d_out && !d_hist) return TSALLIS_ERR_INVALID_ARG;
+    if (nz > 0 && !d_vol) return TSALLIS_ERR_INVALID_ARG;
+    // the kernel copies pixel pairs at even element indices as 4-byte words
+    if ((reinterpret_cast<uintptr_t>(d_vol) & 3) || (reinterpret_cast<uintptr_t>(d_out) & 1))
+        return TSALLIS_ERR_ALIGNMENT;
+    const long long ntx = (nx + preproc_tile_w() - 1) / preproc_tile_w();
+    const long long nty = (ny + preproc_tile_h() - 1) / preproc_tile_h();
+    if (nz > 0 && ntx * nty > 0x7fffffffll / nz) return TSALLIS_ERR_INVALID_ARG;
+    const long long nbytes = nx * ny * nz * (long long)sizeof(int16_t);
+    if (d_out && nz > 0) {
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(d_vol), b0 = reinterpret_cast<uintptr_t>(d_out);
+        if (a0 < b0 + (uintptr_t)nbytes && b0 < a0 + (uintptr_t)nbytes) return TSALLIS_ERR_INVALID_ARG;
+    }
+    PreArgs a;
+    a.D = pp->hu_max - pp->hu_min;
+    if (!level_divider(a.D, &a.magic, &a.shift)) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    const long long nh = pp->per_slice ? nz : 1;
+    if (d_hist && nh > 0 &&
+        cudaMemsetAsync(d_hist, 0, (size_t)nh * 256 * sizeof(int32_t), stream) != cudaSuccess)
+        return TSALLIS_ERR_CUDA;
+    if (nz == 0) return TSALLIS_OK;
+    a.vol = d_vol;
+    a.out = d_out;
+    a.hist = d_hist;
+    a.nx = (int)nx;
+    a.ny = (int)ny;
+    a.nz = (int)nz;
+    a.background = pp->background;
+    a.hu_min = pp->hu_min;
+    a.hu_max = pp->hu_max;
+    a.op = pp->op;
+    a.radius = pp->radius;
+    a.per_slice = pp->per_slice;
+    a.ntx = (int)ntx;
+    a.nty = (int)nty;
+    return cuda_status(launch_preprocess(a, stream));
+}
