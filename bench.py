@@ -345,9 +345,39 @@ def two_d_leg(dev, steps=10, warmup=3):
     assert int(st[0].item()) & 0xff == 0
     peak, _ = _peaks()
     achieved = 5 * vol.numel() / (ms / 1e3) / 1e9
+    # the search alone on this volume's histogram: summed-area tables against
+    # the paper's organisation (one thread per pair, quadrants summed directly)
+    h = tg.tsallis_histogram(vol, p)
+    search = {}
+    for name, pf in (("summed_area", p), ("brute_force", tg.tsallis_params(q=Q, mode="volume", two_d=True,
+                                                                           flags=tg.TSALLIS_FLAG_BRUTE_FORCE_2D))):
+        for _ in range(warmup):
+            r = tg.tsallis_search(h, pf)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            r = tg.tsallis_search(h, pf)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        search[name] = {"ms": e0.elapsed_time(e1) / steps, "t_s": [int(x) for x in r[0][0].tolist()]}
+    # brute force: sum over pairs of the quadrant cells each visits, 2 (sum_{a<L2} a)^2
+    # for L2 = 256; each visit is one integer add and a six-flop FP32 two-sum;
+    # peak 128 FP32 lanes per clock per SM at the maximum SM clock
+    L2 = 256
+    visits = 2 * (L2 * (L2 - 1) // 2) ** 2
+    props = torch.cuda.get_device_properties(dev)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        mhz = 2070.0
+    fp_peak = 128 * props.multi_processor_count * mhz * 1e6 / 1e12
+    fp_ach = 6 * visits / (search["brute_force"]["ms"] / 1e3) / 1e12
+    search["brute_force"]["roofline"] = {"bound": "fp32", "achieved": fp_ach, "peak": fp_peak, "unit": "TFLOP/s",
+                                         "frac": fp_ach / fp_peak, "cell_visits": visits}
     return {"workload": "chest phantom 512x512x256, 2-D grey x 3x3x3 mean, q=0.8, one (t, s) for the volume",
             "value": vol.numel() / (ms / 1e3), "unit": "voxels/s", "ms_per_step": ms, "steps": steps,
-            "t_s": [int(x) for x in t[0].tolist()],
+            "t_s": [int(x) for x in t[0].tolist()], "search_only": search,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "bytes_per_voxel": 5}}
 
@@ -441,6 +471,7 @@ def main():
     ap.add_argument("--preprocess-only", action="store_true",
                     help="print only the pre-processing / chest-mask leg (for profiling)")
     ap.add_argument("--preprocess-nz", type=int, default=NZ, help="slices of the pre-processing leg's volume")
+    ap.add_argument("--two-d-only", action="store_true", help="print only the 2-D leg (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -466,6 +497,10 @@ def main():
     import __graft_entry__
     if rank == 0 or world == 1:
         __graft_entry__.build()
+    if args.two_d_only:
+        torch.cuda.set_device(local)
+        print(json.dumps(two_d_leg(torch.device("cuda", local))), flush=True)
+        return 0
     if args.preprocess_only:
         torch.cuda.set_device(local)
         print(json.dumps(preprocess_leg(torch.device("cuda", local), nz=args.preprocess_nz)), flush=True)

@@ -89,6 +89,17 @@ typedef enum {
  * read carry TSALLIS_STATUS_FIRST_PASS_EXACT. */
 #define TSALLIS_FLAG_PREDICT_PROPOSER 0x2u
 #define TSALLIS_FLAG_PREDICT_SUBSAMPLE 0x4u
+/* 2-D form only (two_d = 1, else TSALLIS_ERR_INVALID_ARG): search as the
+ * paper's GPU code does (section III, Table 4), one thread per threshold
+ * pair (t, s) summing its quadrants directly, O(L2^2) per pair, instead of
+ * through summed-area tables. Counts are exact; terms are FP32 with
+ * compensated sums and each pair's objective is formed in FP64, so values
+ * agree with the default search to about 1e-7 relative; a pair whose value
+ * is within that of another distinct partition's may be chosen instead.
+ * Same outputs, ties (smallest t, then s) and curve as the default search;
+ * no FP64 re-rank (statuses never carry TSALLIS_STATUS_RERANKED). A
+ * comparison point: far slower than the default search. */
+#define TSALLIS_FLAG_BRUTE_FORCE_2D 0x8u
 
 typedef struct {
     int32_t lo;       /* Hounsfield value of level 0, -32768..32767; default -1024 */

@@ -42,6 +42,7 @@ TSALLIS_STATUS_FIRST_PASS_EXACT = 0x200
 TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL = 0x1
 TSALLIS_FLAG_PREDICT_PROPOSER = 0x2
 TSALLIS_FLAG_PREDICT_SUBSAMPLE = 0x4
+TSALLIS_FLAG_BRUTE_FORCE_2D = 0x8
 SLICE_KERNELS = {"auto": 0, "tiles": 1, "cluster": 2}
 
 PER_SLICE, WHOLE_VOLUME = 0, 1

@@ -100,8 +100,10 @@ tsallis_status check_params(const tsallis_params* p) {
         if (p->nbins & ((1 << p->shift) - 1)) return TSALLIS_ERR_INVALID_ARG;   // grey levels must fill [0, L2)
     }
     if (p->topk < 0) return TSALLIS_ERR_INVALID_ARG;
-    if (p->flags & ~(TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL | TSALLIS_FLAG_PREDICT_PROPOSER | TSALLIS_FLAG_PREDICT_SUBSAMPLE))
+    if (p->flags & ~(TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL | TSALLIS_FLAG_PREDICT_PROPOSER | TSALLIS_FLAG_PREDICT_SUBSAMPLE |
+                     TSALLIS_FLAG_BRUTE_FORCE_2D))
         return TSALLIS_ERR_INVALID_ARG;
+    if ((p->flags & TSALLIS_FLAG_BRUTE_FORCE_2D) && !p->two_d) return TSALLIS_ERR_INVALID_ARG;
     return TSALLIS_OK;
 }
 
@@ -343,6 +345,10 @@ tsallis_status ensure_s2(tsallis_ctx* c, size_t bytes) {
 
 constexpr long long kSearch2dChunk = 64;   // histograms per 2-D search launch sequence
 inline int levels2(const tsallis_params* p) { return p->nbins >> p->shift; }
+inline size_t s2_search_bytes(const tsallis_params* p, long long K) {
+    return (p->flags & TSALLIS_FLAG_BRUTE_FORCE_2D) ? search2d_brute_scratch_bytes(levels2(p), K)
+                                                    : search2d_scratch_bytes(levels2(p), K);
+}
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 cudaError_t hist2d_enqueue(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
@@ -384,7 +390,8 @@ cudaError_t search2d_enqueue(tsallis_ctx* c, void* scratch, const int32_t* d_his
         s.t_bin = d_tbin ? d_tbin + k0 : nullptr;
         s.phi = d_phi + k0;
         s.status = d_status + k0;
-        const cudaError_t e = launch_search2d(s, stream);
+        const cudaError_t e = (p->flags & TSALLIS_FLAG_BRUTE_FORCE_2D) ? launch_search2d_brute(s, stream)
+                                                                       : launch_search2d(s, stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -422,7 +429,7 @@ tsallis_status segment2d(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64
     const long long K = ng < kSearch2dChunk ? ng : kSearch2dChunk;
     const size_t hist_bytes = align256((size_t)ng * L2 * L2 * sizeof(int32_t));
     const size_t tbin_bytes = align256((size_t)ng * sizeof(int32_t));
-    const size_t search_bytes = search2d_scratch_bytes(L2, K);
+    const size_t search_bytes = s2_search_bytes(p, K);
     tsallis_status st;
     if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
     if ((st = ensure_s2(c, hist_bytes + tbin_bytes + search_bytes)) != TSALLIS_OK) return st;
@@ -652,7 +659,7 @@ tsallis_status tsallis_search(tsallis_ctx* c, const int32_t* d_hist, int64_t nh,
     if (!g.ok()) return TSALLIS_ERR_CUDA;
     if (p->two_d) {
         const long long K = nh < kSearch2dChunk ? nh : kSearch2dChunk;
-        if ((st = ensure_s2(c, search2d_scratch_bytes(levels2(p), K))) != TSALLIS_OK) return st;
+        if ((st = ensure_s2(c, s2_search_bytes(p, K))) != TSALLIS_OK) return st;
         return cuda_status(search2d_enqueue(c, c->s2_buf, d_hist, nh, p, d_t, nullptr, d_phi, d_status, d_curve,
                                             stream));
     }

@@ -203,6 +203,9 @@ cudaError_t hist2d_occupancy(int* blocks_per_sm);
 cudaError_t launch_hist2d(const Hist2dLaunch& p, cudaStream_t s);
 size_t search2d_scratch_bytes(int L2, long long K);
 cudaError_t launch_search2d(const Search2dLaunch& p, cudaStream_t s);
+// One thread per pair, quadrants summed directly (seg2d_brute.cu).
+size_t search2d_brute_scratch_bytes(int L2, long long K);
+cudaError_t launch_search2d_brute(const Search2dLaunch& p, cudaStream_t s);
 
 // Pre-processing and morphology (preproc.cu): CT numbers to 8-bit levels,
 // flat disk erosion/dilation per slice, chest-mask subtraction, 256-level

@@ -225,3 +225,82 @@ def test_segment2d_chest_full_size():
     """The 2-D workload itself: 512 x 512 x 256, whole volume, 3x3x3 mean, q = 0.8."""
     v = phantom.generate_host(phantom.chest_volume(2012106842, nz=256))
     _check_segment2d(v, "volume", 0.8)
+
+
+# ------------------------------------------------------------ brute-force search (one thread per pair)
+
+BRUTE_GAP = 1e-6     # FP32 terms with compensated sums: values to about 1e-7 relative
+
+
+def _check_pairs_brute(t_g, phi_g, st_g, hs, q, ctx=""):
+    for i, h in enumerate(hs):
+        t, s, best, gap, phi, valid = oracle.search2d(h, f32(q))
+        if t < 0:
+            assert tuple(t_g[i]) == (-1, -1) and (st_g[i] & 0xff) == tg.TSALLIS_ERR_NO_VALID_THRESHOLD, (ctx, i)
+            continue
+        assert st_g[i] == 0, (ctx, i, st_g[i])
+        if gap >= BRUTE_GAP:
+            assert tuple(t_g[i]) == (t, s), (ctx, i, tuple(t_g[i]), (t, s), gap)
+        else:
+            # a near tie: the pair chosen must be valid and within the gap
+            tt, ss = t_g[i]
+            assert valid[tt, ss] and phi[tt, ss] >= best - 2 * BRUTE_GAP * max(abs(best), 1.0), (ctx, i)
+        assert abs(phi_g[i] - best) <= PHI_RTOL * max(abs(best), 1.0), (ctx, i, phi_g[i], best)
+
+
+@pytest.mark.parametrize("q", [0.5, 0.8, 1.0, 1.5, 2.5])
+@pytest.mark.parametrize("L", [2, 3, 16, 33, 256])
+@pytest.mark.parametrize("kind", ["dense", "sparse", "diagonal"])
+def test_brute_force_search_matches_oracle(q, L, kind):
+    rng = np.random.default_rng(L * 37 + int(q * 10) + len(kind))
+    hs = np.stack([_rand_hist2d(rng, L, kind) for _ in range(2)])
+    p = tg.tsallis_params(q=q, two_d=True, nbins=L, shift=0, flags=tg.TSALLIS_FLAG_BRUTE_FORCE_2D)
+    t, phi, st, curve = (x.cpu().numpy() for x in tg.tsallis_search(_cuda(hs), p, curve=True))
+    _check_pairs_brute(t, phi, st, hs, q, (q, L, kind))
+    for i, h in enumerate(hs):
+        ref, valid = oracle.objective2d(h, f32(q))
+        assert np.array_equal(~np.isnan(curve[i]), valid), i
+        d = np.abs(curve[i][valid] - ref[valid])
+        assert np.all(d <= PHI_RTOL * np.maximum(np.abs(ref[valid]), 1.0)), (i, d.max())
+
+
+def test_brute_force_degenerate_many_and_plateaus():
+    """More histograms than one launch chunk, empty and one-bin histograms,
+    and empty rows/columns (plateaus: the smallest (t, s) of a partition)."""
+    L = 12
+    hs = np.zeros((67, L, L), np.int32)
+    hs[0, 3, 3] = 100
+    hs[2, 0, 0] = 5; hs[2, 11, 11] = 5
+    hs[3, 0, 11] = 9; hs[3, 11, 0] = 9
+    rng = np.random.default_rng(17)
+    for k in range(4, 67):
+        h = _rand_hist2d(rng, L, "dense")
+        h[rng.integers(0, L, 3), :] = 0              # empty grey rows
+        h[:, rng.integers(0, L, 3)] = 0              # empty mean columns
+        hs[k] = h
+    for q in (0.8, 1.0, 2.0):
+        p = tg.tsallis_params(q=q, two_d=True, nbins=L, shift=0, flags=tg.TSALLIS_FLAG_BRUTE_FORCE_2D)
+        t, phi, st = (x.cpu().numpy() for x in tg.tsallis_search(_cuda(hs), p))
+        _check_pairs_brute(t, phi, st, hs, q, ("plateau", q))
+
+
+def test_brute_force_agrees_with_summed_area_search_on_phantoms():
+    v = phantom.generate_host(phantom.chest_volume(2012106852, nz=4))
+    hs = _cuda(_oracle_hists(v, "slice").astype(np.int32))
+    for q in (0.5, 0.8, 1.5):
+        p0 = tg.tsallis_params(q=q, two_d=True)
+        pb = tg.tsallis_params(q=q, two_d=True, flags=tg.TSALLIS_FLAG_BRUTE_FORCE_2D)
+        t0, phi0, _ = tg.tsallis_search(hs, p0)
+        tb, phib, stb = tg.tsallis_search(hs, pb)
+        _check_pairs_brute(tb.cpu().numpy(), phib.cpu().numpy(), stb.cpu().numpy(), hs.cpu().numpy(), q, q)
+        assert torch.allclose(phib, phi0, rtol=1e-5, atol=1e-5)
+        # the whole 2-D step with the brute-force search
+        vol = _cuda(v)
+        mb, tb2, _, _ = tg.tsallis_segment(vol, pb)
+        assert torch.equal(tb2, tb)
+
+
+def test_brute_force_flag_needs_two_d():
+    h = torch.zeros((1, 4096), dtype=torch.int32, device="cuda")
+    with pytest.raises(tg.TsallisError):
+        tg.tsallis_search(h, tg.tsallis_params(flags=tg.TSALLIS_FLAG_BRUTE_FORCE_2D))
