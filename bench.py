@@ -375,6 +375,36 @@ def two_d_leg(dev, steps=10, warmup=3):
     fp_ach = 6 * visits / (search["brute_force"]["ms"] / 1e3) / 1e12
     search["brute_force"]["roofline"] = {"bound": "fp32", "achieved": fp_ach, "peak": fp_peak, "unit": "TFLOP/s",
                                          "frac": fp_ach / fp_peak, "cell_visits": visits}
+    # the learned proposer's certified window (16 candidate cells of 4 x 4
+    # pairs), on this volume's histogram and on its 256 slice histograms
+    w2d = os.path.join(ROOT, "paper_2012_10684_gb300", "proposer2d_weights.bin")
+    if os.path.exists(w2d):
+        tg.proposer_select(1, dev)
+        tg.proposer_load(w2d, dev)
+        tg.proposer_select(0, dev)
+        hs = tg.tsallis_histogram(vol, tg.tsallis_params(q=Q, mode="slice", two_d=True))
+        for label, hh in (("volume", h), ("slices", hs)):
+            out = {}
+            for name, pf in (("exhaustive", tg.tsallis_params(q=Q, two_d=True)),
+                             ("window16", tg.tsallis_params(q=Q, two_d=True, topk=16))):
+                for _ in range(warmup):
+                    r = tg.tsallis_search(hh, pf)
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                for _ in range(steps):
+                    r = tg.tsallis_search(hh, pf)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                out[name] = {"ms": e0.elapsed_time(e1) / steps}
+                if name == "window16":
+                    stw = r[2].cpu()
+                    out[name]["hit_rate"] = float(((stw & tg.TSALLIS_STATUS_WINDOW_HIT) != 0).float().mean())
+                    out[name]["mean_cells_searched"] = float(((stw >> tg.TSALLIS_STATUS_FALLBACK_SHIFT) & 0xff)
+                                                             .float().mean())
+                    out[name]["same_as_exhaustive"] = bool(torch.equal(r[0], ref_t))
+                else:
+                    ref_t = r[0]
+            search["proposer_window_" + label] = dict(out, histograms=int(hh.shape[0]))
     return {"workload": "chest phantom 512x512x256, 2-D grey x 3x3x3 mean, q=0.8, one (t, s) for the volume",
             "value": vol.numel() / (ms / 1e3), "unit": "voxels/s", "ms_per_step": ms, "steps": steps,
             "t_s": [int(x) for x in t[0].tolist()], "search_only": search,

@@ -284,7 +284,8 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* ctx, const tsallis_volume* h_v
  *   Setting also clears the optimiser state.
  * tsallis_proposer_load / _save: the same through a file (8-byte magic
  *   "TSPROP01", int64 count, the floats).
- * tsallis_proposer_features: x [nh][256] (device) from histograms [nh][4096].
+ * tsallis_proposer_features: x [nh][256] (device) from histograms [nh][4096]
+ *   (slot 1: from 2-D histograms [nh][256][256]).
  * tsallis_proposer_forward: logits [B][4096] (device) from x [B][256].
  * tsallis_proposer_train_step: forward pass, mean cross-entropy of
  *   softmax(logits) against target distributions y [B][4096] into *d_loss,
@@ -294,6 +295,27 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* ctx, const tsallis_volume* h_v
  *   the stream.
  */
 #define TSALLIS_PROPOSER_PARAMS 1184256
+/*
+ * Two proposers live in a context: slot 0 (the 1-D searches, described
+ * above) and slot 1 (the 2-D search). tsallis_proposer_select chooses the
+ * slot that tsallis_proposer_set, _get, _load, _save, _checkpoint_save,
+ * _checkpoint_load, _features,
+ * _forward and _train_step act on (0 by default); the searches always use their
+ * own slot. Slot 1 has the same network and parameter layout; its features
+ * come from a 2-D histogram of 256 x 256 grey x mean levels:
+ * x_f = log1p(count of 16 x 16 block f) / log1p(N), f = 16 * (grey block) +
+ * (mean block), and its 4096 logits score cells of 4 x 4 threshold pairs,
+ * cell 64 * (t / 4) + s / 4. With params.two_d = 1, nbins >> shift = 256 and
+ * topk = k > 0, tsallis_search / tsallis_segment / tsallis_segment_batch
+ * evaluate the objective at every pair of the k best cells, bound every other
+ * cell from the summed-area tables at its corners (the class counts and term
+ * sums grow with t and s in quadrant 1 and shrink in quadrant 2) and evaluate
+ * the cells whose bound reaches that maximum: the result is the exhaustive
+ * search's. Statuses carry TSALLIS_STATUS_WINDOW_HIT and the number of
+ * searched non-candidate cells (bits 16..23, saturating at 255). Needs slot 1
+ * set; not with TSALLIS_FLAG_BRUTE_FORCE_2D nor a curve output.
+ */
+tsallis_status tsallis_proposer_select(tsallis_ctx* ctx, int32_t slot);
 /*
  * Training checkpoints: tsallis_proposer_checkpoint_save writes the FP32
  * parameters, both Adam moments and the number of Adam steps taken, with a

@@ -22,6 +22,12 @@ to a window of candidates. Its definition, written out here once:
             partition: t* and the empty levels that follow it;
   optimiser Adam (Kingma & Ba 2015) with bias correction.
 
+The 2-D search's proposer is the same network reading a 256 x 256 grey x
+mean histogram: x_f = log1p(count of the 16 x 16 block f) / log1p(N) with
+f = 16 * (grey block) + (mean block), and its 4096 logits score cells of
+4 x 4 threshold pairs, cell 64 * (t // 4) + s // 4; its target is the cell of
+the exact search's pair.
+
 Parameters travel as one flat float vector in the order W1, b1, W2, b2, W3,
 b3, each matrix row-major [out][in].
 """
@@ -147,3 +153,17 @@ def bf16_round(a):
     u = f.view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def features2d(h2):
+    """2-D proposer features [n][256] of 2-D histograms [n][256][256] (zero
+    for an empty histogram)."""
+    h = np.asarray(h2, np.float64).reshape(-1, 256, 256)
+    blocks = h.reshape(-1, 16, 16, 16, 16).sum(axis=(2, 4)).reshape(-1, 256)
+    n = h.reshape(h.shape[0], -1).sum(axis=1, keepdims=True)
+    return np.divide(np.log1p(blocks), np.log1p(n), out=np.zeros_like(blocks), where=n > 0)
+
+
+def cell2d(t, s):
+    """Cell of a 2-D threshold pair: 64 * (t // 4) + s // 4."""
+    return 64 * (np.asarray(t) // 4) + np.asarray(s) // 4

@@ -106,6 +106,7 @@ _SIGS = {
     "tsallis_proposer_load": ([_P, ctypes.c_char_p], ctypes.c_int),
     "tsallis_proposer_save": ([_P, ctypes.c_char_p], ctypes.c_int),
     "tsallis_proposer_features": ([_P, _P, _I64, _P, _P], ctypes.c_int),
+    "tsallis_proposer_select": ([_P, ctypes.c_int32], ctypes.c_int),
     "tsallis_proposer_checkpoint_save": ([_P, ctypes.c_char_p, _P, _I64], ctypes.c_int),
     "tsallis_proposer_checkpoint_load": ([_P, ctypes.c_char_p, _P, _I64, ctypes.POINTER(ctypes.c_int64)],
                                          ctypes.c_int),
@@ -393,11 +394,16 @@ def proposer_save(path: str, device=None) -> None:
     _check("tsallis_proposer_save", lib().tsallis_proposer_save(context(device), os.fsencode(path)))
 
 
+_selected = {}
+
+
 def proposer_features(hist: torch.Tensor) -> torch.Tensor:
-    """x [nh][256] from int32 histograms [nh][4096]."""
-    if not hist.is_cuda or hist.dtype != torch.int32 or not hist.is_contiguous() or hist.numel() % 4096:
-        raise TypeError("hist must be a contiguous int32 CUDA tensor of 4096-level histograms")
-    nh = hist.numel() // 4096
+    """x [nh][256] from int32 histograms [nh][4096] (slot 1 selected:
+    2-D histograms [nh][256][256])."""
+    per = 65536 if _selected.get(hist.device.index, 0) == 1 else 4096
+    if not hist.is_cuda or hist.dtype != torch.int32 or not hist.is_contiguous() or hist.numel() % per:
+        raise TypeError("hist must be a contiguous int32 CUDA tensor of %d-cell histograms" % per)
+    nh = hist.numel() // per
     x = torch.empty((nh, 256), dtype=torch.float32, device=hist.device)
     _check("tsallis_proposer_features", lib().tsallis_proposer_features(context(hist.device), hist.data_ptr(), nh,
                                                                         x.data_ptr(), _stream(hist)))
@@ -465,3 +471,10 @@ def tsallis_preprocess(vol: torch.Tensor, pp: PreprocessParams | None = None, ou
         context(vol.device), vol.data_ptr(), nx, ny, nz, ctypes.byref(pp),
         out.data_ptr() if want_out else None, hist.data_ptr() if want_hist else None, _stream(vol)))
     return (out if want_out else None), (hist if want_hist else None)
+
+
+def proposer_select(slot: int, device=None) -> None:
+    """Slot the proposer_* calls act on: 0 (1-D searches) or 1 (2-D search)."""
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+    _check("tsallis_proposer_select", lib().tsallis_proposer_select(context(dev), int(slot)))
+    _selected[dev] = int(slot)

@@ -15,6 +15,14 @@ using namespace tsl;
 
 static_assert(kMlpParams == TSALLIS_PROPOSER_PARAMS, "parameter count of the C ABI");
 
+struct ProposerSlot {
+    MlpBuffers mlp{};
+    void* params = nullptr;
+    void* act = nullptr;
+    int step = 0;           // Adam steps taken
+    bool ready = false;     // parameters were set
+};
+
 struct tsallis_ctx {
     int device = 0;
     int sm_count = 0;
@@ -50,11 +58,11 @@ struct tsallis_ctx {
     float ptab_q = 0.f;
     // learned proposer: parameters (FP32, bfloat16, gradient, Adam moments),
     // activations for up to mlp.cap rows, features and candidates
-    MlpBuffers mlp{};
-    void* mlp_params = nullptr;
-    void* mlp_act = nullptr;
-    int mlp_step = 0;               // Adam steps taken
-    bool mlp_ready = false;         // parameters were set
+    // slot 0 serves the 1-D searches, slot 1 the 2-D search; the
+    // tsallis_proposer_* calls act on the slot chosen by
+    // tsallis_proposer_select
+    ProposerSlot prop[2];
+    int prop_sel = 0;
     float* prop_x = nullptr;        // [prop_cap][256]
     int32_t* prop_cand = nullptr;   // [prop_cap][256]
     int prop_cap = 0;
@@ -206,47 +214,49 @@ const float2* pow_table(tsallis_ctx* c, long long n, float q, cudaStream_t strea
 
 // Parameter block of the proposer: FP32 copy, gradient, two Adam moments
 // (kMlpParams floats each), then the bfloat16 copy.
-tsallis_status ensure_mlp_params(tsallis_ctx* c) {
-    if (c->mlp_params) return TSALLIS_OK;
+tsallis_status ensure_mlp_params(tsallis_ctx* c, int slot) {
+    ProposerSlot& S = c->prop[slot];
+    if (S.params) return TSALLIS_OK;
     const size_t f = (size_t)kMlpParams * sizeof(float);
     const size_t bytes = 4 * f + (size_t)kMlpParams * 2;
-    if (cudaMalloc(&c->mlp_params, bytes) != cudaSuccess) {
+    if (cudaMalloc(&S.params, bytes) != cudaSuccess) {
         cudaGetLastError();
-        c->mlp_params = nullptr;
+        S.params = nullptr;
         return TSALLIS_ERR_OOM;
     }
-    char* b = static_cast<char*>(c->mlp_params);
-    c->mlp.p32 = reinterpret_cast<float*>(b);
-    c->mlp.grad = reinterpret_cast<float*>(b + f);
-    c->mlp.m = reinterpret_cast<float*>(b + 2 * f);
-    c->mlp.v = reinterpret_cast<float*>(b + 3 * f);
-    c->mlp.p16 = b + 4 * f;
-    if (cudaMemset(c->mlp_params, 0, bytes) != cudaSuccess) return TSALLIS_ERR_CUDA;
+    char* b = static_cast<char*>(S.params);
+    S.mlp.p32 = reinterpret_cast<float*>(b);
+    S.mlp.grad = reinterpret_cast<float*>(b + f);
+    S.mlp.m = reinterpret_cast<float*>(b + 2 * f);
+    S.mlp.v = reinterpret_cast<float*>(b + 3 * f);
+    S.mlp.p16 = b + 4 * f;
+    if (cudaMemset(S.params, 0, bytes) != cudaSuccess) return TSALLIS_ERR_CUDA;
     return TSALLIS_OK;
 }
 
 // Activations for `rows` rows of the proposer (grown, never shrunk; the
 // device is synchronised before a smaller buffer is replaced).
-tsallis_status ensure_mlp_act(tsallis_ctx* c, int rows) {
-    if (c->mlp_act && c->mlp.cap >= rows) return TSALLIS_OK;
-    int cap = c->mlp.cap > 0 ? c->mlp.cap : 256;
+tsallis_status ensure_mlp_act(tsallis_ctx* c, int slot, int rows) {
+    ProposerSlot& S = c->prop[slot];
+    if (S.act && S.mlp.cap >= rows) return TSALLIS_OK;
+    int cap = S.mlp.cap > 0 ? S.mlp.cap : 256;
     while (cap < rows) cap *= 2;
-    if (c->mlp_act) {
+    if (S.act) {
         if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
-        cudaFree(c->mlp_act);
-        c->mlp_act = nullptr;
-        c->mlp.cap = 0;
+        cudaFree(S.act);
+        S.act = nullptr;
+        S.mlp.cap = 0;
     }
     const size_t h = (size_t)cap * kMlpHid, o = (size_t)cap * kMlpOut;
-    if (cudaMalloc(&c->mlp_act, (6 * h + 2 * o) * sizeof(float)) != cudaSuccess) {
+    if (cudaMalloc(&S.act, (6 * h + 2 * o) * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return TSALLIS_ERR_OOM;
     }
-    float* f = static_cast<float*>(c->mlp_act);
-    c->mlp.z1 = f; c->mlp.a1 = f + h; c->mlp.z2 = f + 2 * h; c->mlp.a2 = f + 3 * h;
-    c->mlp.da = f + 4 * h; c->mlp.dz = f + 5 * h;
-    c->mlp.z3 = f + 6 * h; c->mlp.d3 = f + 6 * h + o;
-    c->mlp.cap = cap;
+    float* f = static_cast<float*>(S.act);
+    S.mlp.z1 = f; S.mlp.a1 = f + h; S.mlp.z2 = f + 2 * h; S.mlp.a2 = f + 3 * h;
+    S.mlp.da = f + 4 * h; S.mlp.dz = f + 5 * h;
+    S.mlp.z3 = f + 6 * h; S.mlp.d3 = f + 6 * h + o;
+    S.mlp.cap = cap;
     return TSALLIS_OK;
 }
 
@@ -276,17 +286,18 @@ tsallis_status ensure_prop(tsallis_ctx* c, int rows) {
 // levels, then the certified window search (search1d.cuh).
 tsallis_status search_window(tsallis_ctx* c, const int32_t* d_hist, long long nh, const tsallis_params* p,
                              int32_t* d_t, float* d_phi, int32_t* d_status, cudaStream_t stream) {
-    if (!c->mlp_ready) return TSALLIS_ERR_INVALID_ARG;   // no proposer was set
+    ProposerSlot& S = c->prop[0];
+    if (!S.ready) return TSALLIS_ERR_INVALID_ARG;   // no proposer was set
     if (p->nbins != kMlpOut || p->two_d || p->topk < 1 || p->topk > 256) return TSALLIS_ERR_INVALID_ARG;
     tsallis_status st;
     const int chunk = (int)(nh < kPropChunk ? nh : kPropChunk);
-    if ((st = ensure_mlp_act(c, chunk)) != TSALLIS_OK || (st = ensure_prop(c, chunk)) != TSALLIS_OK) return st;
+    if ((st = ensure_mlp_act(c, 0, chunk)) != TSALLIS_OK || (st = ensure_prop(c, chunk)) != TSALLIS_OK) return st;
     for (long long h0 = 0; h0 < nh; h0 += chunk) {
         const int n = (int)(nh - h0 < chunk ? nh - h0 : chunk);
         const int32_t* hist = d_hist + h0 * kMlpOut;
         if (mlp_features(hist, n, c->prop_x, stream) != cudaSuccess ||
-            mlp_forward(c->mlp, c->prop_x, n, stream) != cudaSuccess ||
-            mlp_topk(c->mlp.z3, n, p->topk, c->prop_cand, stream) != cudaSuccess ||
+            mlp_forward(S.mlp, c->prop_x, n, stream) != cudaSuccess ||
+            mlp_topk(S.mlp.z3, n, p->topk, c->prop_cand, stream) != cudaSuccess ||
             launch_search1d_window(hist, n, kMlpOut, p->q, c->prop_cand, p->topk, d_t + h0, d_phi + h0,
                                    d_status + h0, c->df_tables, stream) != cudaSuccess)
             return TSALLIS_ERR_CUDA;
@@ -345,11 +356,24 @@ tsallis_status ensure_s2(tsallis_ctx* c, size_t bytes) {
 
 constexpr long long kSearch2dChunk = 64;   // histograms per 2-D search launch sequence
 inline int levels2(const tsallis_params* p) { return p->nbins >> p->shift; }
+// the 2-D window search's cell flags and counts follow the search tables
+inline size_t s2_window_bytes(const tsallis_params* p, long long K) {
+    return p->topk > 0 ? (size_t)K * kCells2d + (size_t)K * sizeof(int) + 512 : 0;
+}
 inline size_t s2_search_bytes(const tsallis_params* p, long long K) {
-    return (p->flags & TSALLIS_FLAG_BRUTE_FORCE_2D) ? search2d_brute_scratch_bytes(levels2(p), K)
-                                                    : search2d_scratch_bytes(levels2(p), K);
+    return ((p->flags & TSALLIS_FLAG_BRUTE_FORCE_2D) ? search2d_brute_scratch_bytes(levels2(p), K)
+                                                     : search2d_scratch_bytes(levels2(p), K)) +
+           s2_window_bytes(p, K);
 }
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// The 2-D window search needs the 2-D proposer (slot 1) and 256 grey levels.
+tsallis_status check_window2d(tsallis_ctx* c, const tsallis_params* p) {
+    if (p->topk <= 0) return TSALLIS_OK;
+    if (!c->prop[1].ready || levels2(p) != 256 || p->topk > 256 || (p->flags & TSALLIS_FLAG_BRUTE_FORCE_2D))
+        return TSALLIS_ERR_INVALID_ARG;
+    return TSALLIS_OK;
+}
 
 cudaError_t hist2d_enqueue(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
                            const tsallis_params* p, int32_t* d_hist, long long nh, cudaStream_t stream) {
@@ -377,8 +401,16 @@ cudaError_t search2d_enqueue(tsallis_ctx* c, void* scratch, const int32_t* d_his
                              float* d_curve, cudaStream_t stream) {
     const int L2 = levels2(p);
     const long long cells = (long long)L2 * L2, m2 = (long long)(L2 - 1) * (L2 - 1);
+    const bool window = p->topk > 0;
+    const long long Kmax = nh < kSearch2dChunk ? nh : kSearch2dChunk;
+    unsigned char* wbuf = nullptr;
+    if (window) {
+        if (ensure_mlp_act(c, 1, (int)Kmax) != TSALLIS_OK || ensure_prop(c, (int)Kmax) != TSALLIS_OK)
+            return cudaErrorMemoryAllocation;
+        wbuf = static_cast<unsigned char*>(scratch) + search2d_scratch_bytes(L2, Kmax);
+    }
     for (long long k0 = 0; k0 < nh; k0 += kSearch2dChunk) {
-        Search2dLaunch s;
+        Search2dLaunch s{};
         s.K = nh - k0 < kSearch2dChunk ? nh - k0 : kSearch2dChunk;
         s.hist = d_hist + k0 * cells;
         s.L2 = L2;
@@ -390,8 +422,25 @@ cudaError_t search2d_enqueue(tsallis_ctx* c, void* scratch, const int32_t* d_his
         s.t_bin = d_tbin ? d_tbin + k0 : nullptr;
         s.phi = d_phi + k0;
         s.status = d_status + k0;
-        const cudaError_t e = (p->flags & TSALLIS_FLAG_BRUTE_FORCE_2D) ? launch_search2d_brute(s, stream)
-                                                                       : launch_search2d(s, stream);
+        cudaError_t e;
+        if (p->flags & TSALLIS_FLAG_BRUTE_FORCE_2D) {
+            e = launch_search2d_brute(s, stream);
+        } else if (window) {
+            // tables, then the proposer's candidate cells and the cells whose
+            // bound reaches them, then evaluation of the flagged cells only
+            s.topk = p->topk;
+            s.cand = c->prop_cand;
+            s.cellflag = wbuf;
+            s.winfo = reinterpret_cast<int*>(wbuf + align256((size_t)Kmax * kCells2d));
+            e = launch_search2d_tables(s, stream);
+            if (e == cudaSuccess) e = mlp_features2d(s.hist, s.K, c->prop_x, stream);
+            if (e == cudaSuccess) e = mlp_forward(c->prop[1].mlp, c->prop_x, (int)s.K, stream);
+            if (e == cudaSuccess) e = mlp_topk(c->prop[1].mlp.z3, (int)s.K, p->topk, c->prop_cand, stream);
+            if (e == cudaSuccess) e = launch_search2d_window(s, stream);
+            if (e == cudaSuccess) e = launch_search2d_finish(s, stream);
+        } else {
+            e = launch_search2d(s, stream);
+        }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -430,7 +479,8 @@ tsallis_status segment2d(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64
     const size_t hist_bytes = align256((size_t)ng * L2 * L2 * sizeof(int32_t));
     const size_t tbin_bytes = align256((size_t)ng * sizeof(int32_t));
     const size_t search_bytes = s2_search_bytes(p, K);
-    tsallis_status st;
+    tsallis_status st = check_window2d(c, p);
+    if (st != TSALLIS_OK) return st;
     if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
     if ((st = ensure_s2(c, hist_bytes + tbin_bytes + search_bytes)) != TSALLIS_OK) return st;
     unsigned char* b = static_cast<unsigned char*>(c->s2_buf);
@@ -575,8 +625,10 @@ void tsallis_destroy(tsallis_ctx* c) {
         if (c->df_tables) cudaFree(c->df_tables);
         if (c->log2_table) cudaFree(c->log2_table);
         if (c->ptab) cudaFree(c->ptab);
-        if (c->mlp_params) cudaFree(c->mlp_params);
-        if (c->mlp_act) cudaFree(c->mlp_act);
+        for (ProposerSlot& S : c->prop) {
+            if (S.params) cudaFree(S.params);
+            if (S.act) cudaFree(S.act);
+        }
         if (c->prop_x) cudaFree(c->prop_x);
         if (c->pred_buf) cudaFree(c->pred_buf);
     }
@@ -658,6 +710,8 @@ tsallis_status tsallis_search(tsallis_ctx* c, const int32_t* d_hist, int64_t nh,
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
     if (p->two_d) {
+        if ((st = check_window2d(c, p)) != TSALLIS_OK) return st;
+        if (p->topk > 0 && d_curve) return TSALLIS_ERR_INVALID_ARG;   // the window evaluates only some pairs
         const long long K = nh < kSearch2dChunk ? nh : kSearch2dChunk;
         if ((st = ensure_s2(c, s2_search_bytes(p, K))) != TSALLIS_OK) return st;
         return cuda_status(search2d_enqueue(c, c->s2_buf, d_hist, nh, p, d_t, nullptr, d_phi, d_status, d_curve,
@@ -805,6 +859,7 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
     if (!c || nvol < 0) return TSALLIS_ERR_INVALID_ARG;
     if (nvol == 0) return TSALLIS_OK;
     if (!h_vols || !d_t || !d_phi || !d_status) return TSALLIS_ERR_INVALID_ARG;
+    ProposerSlot& S = c->prop[0];
     // validate every volume and lay out its groups and tiles
     std::vector<BatchVolDesc> vd((size_t)nvol);
     long long ng = 0, ntot = 0;
@@ -842,7 +897,7 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
     }
     const unsigned predict = p->flags & (TSALLIS_FLAG_PREDICT_PROPOSER | TSALLIS_FLAG_PREDICT_SUBSAMPLE);
     if (predict && (p->mode != TSALLIS_WHOLE_VOLUME || p->topk > 0 ||
-                    ((predict & TSALLIS_FLAG_PREDICT_PROPOSER) && (!c->mlp_ready || p->nbins != kMlpOut))))
+                    ((predict & TSALLIS_FLAG_PREDICT_PROPOSER) && (!S.ready || p->nbins != kMlpOut))))
         return TSALLIS_ERR_INVALID_ARG;
     const bool spec = c->speculate || predict;
     // exception lists only for the speculation setting: with a prediction per
@@ -882,7 +937,7 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
         // window search: histograms, proposer + certified window search,
         // then Algorithm 1 (three launches; volumes are read twice as in
         // the one-launch path)
-        if (!c->mlp_ready || p->nbins != kMlpOut) return TSALLIS_ERR_INVALID_ARG;
+        if (!S.ready || p->nbins != kMlpOut) return TSALLIS_ERR_INVALID_ARG;
         ScratchView sv = view(c);
         const size_t hb = (size_t)ng * kMaxLevels * sizeof(int);
         SegArgs h;
@@ -965,10 +1020,10 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
             launch_segment1d(h, grid_for(c, h.ntotal), c->copies, stream) != cudaSuccess)
             return TSALLIS_ERR_CUDA;
         if (predict & TSALLIS_FLAG_PREDICT_PROPOSER) {
-            if ((st = ensure_mlp_act(c, nvol)) != TSALLIS_OK || (st = ensure_prop(c, nvol)) != TSALLIS_OK) return st;
+            if ((st = ensure_mlp_act(c, 0, nvol)) != TSALLIS_OK || (st = ensure_prop(c, nvol)) != TSALLIS_OK) return st;
             if (mlp_features(sh, nvol, c->prop_x, stream) != cudaSuccess ||
-                mlp_forward(c->mlp, c->prop_x, nvol, stream) != cudaSuccess ||
-                mlp_topk(c->mlp.z3, nvol, 1, ht, stream) != cudaSuccess)
+                mlp_forward(S.mlp, c->prop_x, nvol, stream) != cudaSuccess ||
+                mlp_topk(S.mlp.z3, nvol, 1, ht, stream) != cudaSuccess)
                 return TSALLIS_ERR_CUDA;
         } else if (launch_search1d(sh, nvol, p->nbins, p->q, ht, hphi, hst, nullptr, c->df_tables, stream) !=
                    cudaSuccess) {
@@ -1009,27 +1064,31 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
 }
 
 tsallis_status tsallis_proposer_set(tsallis_ctx* c, const float* h_params, int64_t n) {
-    if (!c || !h_params || n != kMlpParams) return TSALLIS_ERR_INVALID_ARG;
+    if (!c) return TSALLIS_ERR_INVALID_ARG;
+    ProposerSlot& S = c->prop[c->prop_sel];
+    if (!h_params || n != kMlpParams) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
-    tsallis_status st = ensure_mlp_params(c);
+    tsallis_status st = ensure_mlp_params(c, c->prop_sel);
     if (st != TSALLIS_OK) return st;
     const size_t f = (size_t)kMlpParams * sizeof(float);
-    if (cudaMemcpy(c->mlp.p32, h_params, f, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(c->mlp.m, 0, f) != cudaSuccess || cudaMemset(c->mlp.v, 0, f) != cudaSuccess ||
-        mlp_to_bf16(c->mlp.p32, c->mlp.p16, kMlpParams, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    if (cudaMemcpy(S.mlp.p32, h_params, f, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(S.mlp.m, 0, f) != cudaSuccess || cudaMemset(S.mlp.v, 0, f) != cudaSuccess ||
+        mlp_to_bf16(S.mlp.p32, S.mlp.p16, kMlpParams, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
         return TSALLIS_ERR_CUDA;
-    c->mlp_step = 0;
-    c->mlp_ready = true;
+    S.step = 0;
+    S.ready = true;
     return TSALLIS_OK;
 }
 
 tsallis_status tsallis_proposer_get(tsallis_ctx* c, float* h_params, int64_t n) {
-    if (!c || !h_params || n != kMlpParams || !c->mlp_ready) return TSALLIS_ERR_INVALID_ARG;
+    if (!c) return TSALLIS_ERR_INVALID_ARG;
+    ProposerSlot& S = c->prop[c->prop_sel];
+    if (!h_params || n != kMlpParams || !S.ready) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
     if (cudaDeviceSynchronize() != cudaSuccess ||
-        cudaMemcpy(h_params, c->mlp.p32, (size_t)kMlpParams * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(h_params, S.mlp.p32, (size_t)kMlpParams * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
         return TSALLIS_ERR_CUDA;
     return TSALLIS_OK;
 }
@@ -1057,7 +1116,9 @@ tsallis_status tsallis_proposer_load(tsallis_ctx* c, const char* path) {
 }
 
 tsallis_status tsallis_proposer_save(tsallis_ctx* c, const char* path) {
-    if (!c || !path || !c->mlp_ready) return TSALLIS_ERR_INVALID_ARG;
+    if (!c) return TSALLIS_ERR_INVALID_ARG;
+    ProposerSlot& S = c->prop[c->prop_sel];
+    if (!path || !S.ready) return TSALLIS_ERR_INVALID_ARG;
     std::vector<float> buf((size_t)kMlpParams);
     tsallis_status st = tsallis_proposer_get(c, buf.data(), kMlpParams);
     if (st != TSALLIS_OK) return st;
@@ -1097,15 +1158,17 @@ struct CkptHeader {
 
 tsallis_status tsallis_proposer_checkpoint_save(tsallis_ctx* c, const char* path, const void* user,
                                                 int64_t user_bytes) {
-    if (!c || !path || !c->mlp_ready || user_bytes < 0 || (user_bytes > 0 && !user)) return TSALLIS_ERR_INVALID_ARG;
+    if (!c) return TSALLIS_ERR_INVALID_ARG;
+    ProposerSlot& S = c->prop[c->prop_sel];
+    if (!path || !S.ready || user_bytes < 0 || (user_bytes > 0 && !user)) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
     const size_t f = (size_t)kMlpParams * sizeof(float);
     std::vector<float> buf(3 * (size_t)kMlpParams);
     if (cudaDeviceSynchronize() != cudaSuccess ||
-        cudaMemcpy(buf.data(), c->mlp.p32, f, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(buf.data() + kMlpParams, c->mlp.m, f, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(buf.data() + 2 * kMlpParams, c->mlp.v, f, cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(buf.data(), S.mlp.p32, f, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(buf.data() + kMlpParams, S.mlp.m, f, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(buf.data() + 2 * kMlpParams, S.mlp.v, f, cudaMemcpyDeviceToHost) != cudaSuccess)
         return TSALLIS_ERR_CUDA;
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
@@ -1115,7 +1178,7 @@ tsallis_status tsallis_proposer_checkpoint_save(tsallis_ctx* c, const char* path
     h.nhid = kMlpHid;
     h.nout = kMlpOut;
     h.nparams = kMlpParams;
-    h.step = c->mlp_step;
+    h.step = S.step;
     h.user_bytes = user_bytes;
     uint32_t crc = crc32_update(0, &h, sizeof(h));
     crc = crc32_update(crc, buf.data(), buf.size() * sizeof(float));
@@ -1132,7 +1195,9 @@ tsallis_status tsallis_proposer_checkpoint_save(tsallis_ctx* c, const char* path
 
 tsallis_status tsallis_proposer_checkpoint_load(tsallis_ctx* c, const char* path, void* user, int64_t user_cap,
                                                 int64_t* user_bytes) {
-    if (!c || !path || user_cap < 0 || (user_cap > 0 && !user)) return TSALLIS_ERR_INVALID_ARG;
+    if (!c) return TSALLIS_ERR_INVALID_ARG;
+    ProposerSlot& S = c->prop[c->prop_sel];
+    if (!path || user_cap < 0 || (user_cap > 0 && !user)) return TSALLIS_ERR_INVALID_ARG;
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return TSALLIS_ERR_INVALID_ARG;
     CkptHeader h;
@@ -1161,10 +1226,10 @@ tsallis_status tsallis_proposer_checkpoint_load(tsallis_ctx* c, const char* path
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
     const size_t f = (size_t)kMlpParams * sizeof(float);
-    if (cudaMemcpy(c->mlp.m, buf.data() + kMlpParams, f, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c->mlp.v, buf.data() + 2 * kMlpParams, f, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(S.mlp.m, buf.data() + kMlpParams, f, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(S.mlp.v, buf.data() + 2 * kMlpParams, f, cudaMemcpyHostToDevice) != cudaSuccess)
         return TSALLIS_ERR_CUDA;
-    c->mlp_step = (int)h.step;
+    S.step = (int)h.step;
     if (!ub.empty()) std::memcpy(user, ub.data(), ub.size());
     if (user_bytes) *user_bytes = h.user_bytes;
     return TSALLIS_OK;
@@ -1175,19 +1240,28 @@ tsallis_status tsallis_proposer_features(tsallis_ctx* c, const int32_t* d_hist, 
     if (!c || nh < 0 || (nh > 0 && (!d_hist || !d_x))) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
-    return cuda_status(mlp_features(d_hist, nh, d_x, stream));
+    return cuda_status(c->prop_sel == 1 ? mlp_features2d(d_hist, nh, d_x, stream)
+                                        : mlp_features(d_hist, nh, d_x, stream));
+}
+
+tsallis_status tsallis_proposer_select(tsallis_ctx* c, int32_t slot) {
+    if (!c || (slot != 0 && slot != 1)) return TSALLIS_ERR_INVALID_ARG;
+    c->prop_sel = slot;
+    return TSALLIS_OK;
 }
 
 tsallis_status tsallis_proposer_forward(tsallis_ctx* c, const float* d_x, int32_t B, float* d_logits,
                                         cudaStream_t stream) {
-    if (!c || B < 0 || (B > 0 && (!d_x || !d_logits)) || !c->mlp_ready) return TSALLIS_ERR_INVALID_ARG;
+    if (!c) return TSALLIS_ERR_INVALID_ARG;
+    ProposerSlot& S = c->prop[c->prop_sel];
+    if (B < 0 || (B > 0 && (!d_x || !d_logits)) || !S.ready) return TSALLIS_ERR_INVALID_ARG;
     if (B == 0) return TSALLIS_OK;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
-    tsallis_status st = ensure_mlp_act(c, B);
+    tsallis_status st = ensure_mlp_act(c, c->prop_sel, B);
     if (st != TSALLIS_OK) return st;
-    if (mlp_forward(c->mlp, d_x, B, stream) != cudaSuccess ||
-        cudaMemcpyAsync(d_logits, c->mlp.z3, (size_t)B * kMlpOut * sizeof(float), cudaMemcpyDeviceToDevice,
+    if (mlp_forward(S.mlp, d_x, B, stream) != cudaSuccess ||
+        cudaMemcpyAsync(d_logits, S.mlp.z3, (size_t)B * kMlpOut * sizeof(float), cudaMemcpyDeviceToDevice,
                         stream) != cudaSuccess)
         return TSALLIS_ERR_CUDA;
     return TSALLIS_OK;
@@ -1195,20 +1269,22 @@ tsallis_status tsallis_proposer_forward(tsallis_ctx* c, const float* d_x, int32_
 
 tsallis_status tsallis_proposer_train_step(tsallis_ctx* c, const float* d_x, const float* d_y, int32_t B, float lr,
                                            int32_t update, float* d_loss, float* d_grad, cudaStream_t stream) {
-    if (!c || B < 1 || !d_x || !d_y || !d_loss || !c->mlp_ready || !(lr >= 0.f)) return TSALLIS_ERR_INVALID_ARG;
+    if (!c) return TSALLIS_ERR_INVALID_ARG;
+    ProposerSlot& S = c->prop[c->prop_sel];
+    if (B < 1 || !d_x || !d_y || !d_loss || !S.ready || !(lr >= 0.f)) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
-    tsallis_status st = ensure_mlp_act(c, B);
+    tsallis_status st = ensure_mlp_act(c, c->prop_sel, B);
     if (st != TSALLIS_OK) return st;
-    if (mlp_forward(c->mlp, d_x, B, stream) != cudaSuccess ||
-        mlp_backward(c->mlp, d_x, d_y, B, d_loss, stream) != cudaSuccess)
+    if (mlp_forward(S.mlp, d_x, B, stream) != cudaSuccess ||
+        mlp_backward(S.mlp, d_x, d_y, B, d_loss, stream) != cudaSuccess)
         return TSALLIS_ERR_CUDA;
-    if (d_grad && cudaMemcpyAsync(d_grad, c->mlp.grad, (size_t)kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice,
+    if (d_grad && cudaMemcpyAsync(d_grad, S.mlp.grad, (size_t)kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice,
                                   stream) != cudaSuccess)
         return TSALLIS_ERR_CUDA;
     if (update) {
-        c->mlp_step += 1;
-        if (mlp_adam(c->mlp, lr, c->mlp_step, stream) != cudaSuccess) return TSALLIS_ERR_CUDA;
+        S.step += 1;
+        if (mlp_adam(S.mlp, lr, S.step, stream) != cudaSuccess) return TSALLIS_ERR_CUDA;
     }
     return TSALLIS_OK;
 }

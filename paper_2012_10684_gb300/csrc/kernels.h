@@ -167,6 +167,7 @@ struct MlpBuffers {
     int cap;
 };
 cudaError_t mlp_features(const int32_t* hist, long long nh, float* x, cudaStream_t s);
+cudaError_t mlp_features2d(const int32_t* hist, long long nh, float* x, cudaStream_t s);   // [nh][256][256]
 cudaError_t mlp_to_bf16(const float* p, void* p16, long long n, cudaStream_t s);
 cudaError_t mlp_forward(const MlpBuffers& b, const float* x, int B, cudaStream_t s);   // logits in b.z3
 cudaError_t mlp_backward(const MlpBuffers& b, const float* x, const float* y, int B, float* loss, cudaStream_t s);
@@ -185,6 +186,9 @@ struct Hist2dLaunch {
     int* hist;              // [nh][L2][L2], zeroed by the caller
     int sm_count, blocks_per_sm;
 };
+// 2-D window search: cells of 4 x 4 pairs, 64 x 64 of them for 256 levels.
+constexpr int kCell2d = 4;
+constexpr int kCells2d = 4096;
 struct Search2dLaunch {
     const int* hist;        // [K][L2][L2]
     long long K;
@@ -197,12 +201,24 @@ struct Search2dLaunch {
     int* t_bin;             // optional [K]
     float* phi;
     int* status;
+    // window search (optional): per histogram, the proposer's candidate
+    // cells [K][topk], a flag per cell [K][kCells2d] (0 skip, 1 bound
+    // reaches the window, 2 candidate) and the number of flag-1 cells [K]
+    const int* cand;
+    int topk;
+    unsigned char* cellflag;
+    int* winfo;
 };
 cudaError_t seg2d_prepare();
 cudaError_t hist2d_occupancy(int* blocks_per_sm);
 cudaError_t launch_hist2d(const Hist2dLaunch& p, cudaStream_t s);
 size_t search2d_scratch_bytes(int L2, long long K);
 cudaError_t launch_search2d(const Search2dLaunch& p, cudaStream_t s);
+// the same in phases: tables (row and column scans), then, for a window
+// search, the cell flags, then evaluation and the final maximum
+cudaError_t launch_search2d_tables(const Search2dLaunch& p, cudaStream_t s);
+cudaError_t launch_search2d_window(const Search2dLaunch& p, cudaStream_t s);
+cudaError_t launch_search2d_finish(const Search2dLaunch& p, cudaStream_t s);
 // One thread per pair, quadrants summed directly (seg2d_brute.cu).
 size_t search2d_brute_scratch_bytes(int L2, long long K);
 cudaError_t launch_search2d_brute(const Search2dLaunch& p, cudaStream_t s);

@@ -254,7 +254,39 @@ __global__ void __launch_bounds__(512) k_topk(const float* __restrict__ z, int k
         out[(long long)row * k + i] = (int32_t)(0xffffffffu - (unsigned)(key[i] & 0xffffffffu));
 }
 
+// 2-D form: x_f = log1p(count of the 16 x 16 block f of the 256 x 256
+// grey x mean histogram) / log1p(N), f = 16 * (grey block) + mean block.
+__global__ void __launch_bounds__(kMlpIn) k_features2d(const int32_t* __restrict__ hist, long long nh,
+                                                         float* __restrict__ x) {
+    __shared__ long long part[kMlpIn / 32];
+    const int bi = threadIdx.x >> 4, bj = threadIdx.x & 15;
+    for (long long h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int32_t* r = hist + h * 65536ll + (bi * 16) * 256 + bj * 16;
+        long long s = 0;
+        for (int i = 0; i < 16; ++i)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) s += r[i * 256 + j];
+        long long w = s;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = w;
+        __syncthreads();
+        long long n = 0;
+#pragma unroll
+        for (int i = 0; i < kMlpIn / 32; ++i) n += part[i];
+        __syncthreads();
+        const float den = log1pf((float)n);
+        x[h * kMlpIn + threadIdx.x] = n > 0 ? log1pf((float)s) / den : 0.f;
+    }
+}
+
 }  // namespace
+
+cudaError_t mlp_features2d(const int32_t* hist, long long nh, float* x, cudaStream_t s) {
+    if (nh <= 0) return cudaSuccess;
+    k_features2d<<<(int)(nh < 65535 ? nh : 65535), kMlpIn, 0, s>>>(hist, nh, x);
+    return cudaGetLastError();
+}
 
 cudaError_t mlp_features(const int32_t* hist, long long nh, float* x, cudaStream_t s) {
     if (nh <= 0) return cudaSuccess;

@@ -241,6 +241,11 @@ struct S2Args {
     int* t_bin;           // optional [K]: t alone, for the binarise pass
     float* phi_out;
     int* status;
+    // window search (null / 0 otherwise)
+    const int* cand;      // [K][topk] candidate cells
+    int topk;
+    unsigned char* cellflag;   // [K][kCells2d]
+    int* winfo;           // [K] cells searched beyond the candidates
 };
 
 __device__ __forceinline__ long long s2_off(const S2Args& a, int k) { return (long long)k * a.L2 * a.L2; }
@@ -456,11 +461,13 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_eval(const S2Args a) {
     F2 phi{0.f, 0.f};
     float band = 0.f;
     bool ok = false;
-    if (s < m) {
+    const bool wanted = !a.cellflag || a.cellflag[(long long)k * kCells2d + (t / kCell2d) * 64 + s / kCell2d];
+    if (s < m && wanted) {
         ok = eval_df(quad_sums(a, k, t, s), a.q, a.T, phi, band);
         if (ok) tp = Top{phi, t * m + s, band, -INFINITY};
     }
-    if (a.curve && s < m) a.curve[((long long)k * m + t) * m + s] = ok ? phi.hi + phi.lo : __int_as_float(0x7fc00000);
+    if (a.curve && s < m && wanted)
+        a.curve[((long long)k * m + t) * m + s] = ok ? phi.hi + phi.lo : __int_as_float(0x7fc00000);
     const Top g = block_top2(tp, sm);
     if (s == 0) {
         const long long r = (long long)k * a.L2 + t;
@@ -502,6 +509,110 @@ constexpr double kSamePartitionTol = 1e-10;
 // pair's bound reaches it, the pairs inside the bounds are re-ranked in FP64,
 // and among pairs with the winner's quadrant counts and value the smallest
 // (t, s) is returned.
+// Status bits of a window search: the winner's cell among the candidates,
+// and how many other cells had to be searched (saturating at 255).
+__device__ __forceinline__ int window_bits(const S2Args& a, int k, int t, int s) {
+    if (!a.cellflag) return 0;
+    const int hit = a.cellflag[(long long)k * kCells2d + (t / kCell2d) * 64 + s / kCell2d] == 2;
+    return (hit ? TSALLIS_STATUS_WINDOW_HIT : 0) | (min(a.winfo[k], 255) << TSALLIS_STATUS_FALLBACK_SHIFT);
+}
+
+// Upper bound of phi over the valid pairs of the cell [t0, t1] x [s0, s1]
+// from the tables at its corners: N_1, Q_1 grow and N_2, Q_2 shrink with t
+// and with s, so for q < 1 a b <= Q_1(t1,s1) Q_2(t0,s0) / (N_1(t0,s0)
+// N_2(t1,s1))^q, for q > 1 a b >= Q_1(t0,s0) Q_2(t1,s1) / (N_1(t1,s1)
+// N_2(t0,s0))^q, and at q = 1 each H_k <= log N_k(max) - Q_k(min) / N_k(max).
+// Evaluated in double-float like the objective (FP32 instructions; FP64 is
+// slow on this part); -inf when the cell holds no valid pair, +inf when a
+// bound is unbounded.
+__device__ float cell_bound(const S2Args& a, int k, int t0, int t1, int s0, int s1) {
+    const long long o = s2_off(a, k);
+    const long long a0 = o + (long long)t0 * a.L2 + s0, a1 = o + (long long)t1 * a.L2 + s1;
+    const long long b_big = o + (long long)(t0 + 1) * a.L2 + (s0 + 1), b_small = o + (long long)(t1 + 1) * a.L2 + (s1 + 1);
+    const int na0 = a.PC[a0], na1 = a.PC[a1], nb1 = a.SC[b_big], nb0 = a.SC[b_small];
+    if (na1 <= 0 || nb1 <= 0) return -INFINITY;
+    const float2 qa0f = a.PW[a0], qa1f = a.PW[a1], qb1f = a.SW[b_big], qb0f = a.SW[b_small];
+    const F2 qa0{qa0f.x, qa0f.y}, qa1{qa1f.x, qa1f.y}, qb0{qb0f.x, qb0f.y}, qb1{qb1f.x, qb1f.y};
+    if (a.q == 1.0f) {
+        const F2 la = df_log2_count<true>((unsigned)na1, a.T), lb = df_log2_count<true>((unsigned)nb1, a.T);
+        const F2 sa = df_div(qa0, df_from_u32((unsigned)na1)), sb = df_div(qb0, df_from_u32((unsigned)nb1));
+        const F2 phi = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
+        return phi.hi + phi.lo;
+    }
+    const F2 LN{kFixedLog2N, 0.f};
+    F2 ab;
+    if (a.q < 1.0f) {
+        if (na0 <= 0 || nb0 <= 0) return INFINITY;
+        const F2 pa = df_pow_ratio<true>((unsigned)na0, LN, a.q, a.T), pb = df_pow_ratio<true>((unsigned)nb0, LN, a.q, a.T);
+        ab = df_mul(df_div(qa1, pa), df_div(qb1, pb));
+    } else {
+        const F2 pa = df_pow_ratio<true>((unsigned)na1, LN, a.q, a.T), pb = df_pow_ratio<true>((unsigned)nb1, LN, a.q, a.T);
+        ab = df_mul(df_div(qa0, pa), df_div(qb0, pb));
+    }
+    const F2 phi = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), two_sum(a.q, -1.0f));
+    return phi.hi + phi.lo;
+}
+
+constexpr int kWindowParts = kCells2d / kS2Threads;   // blocks per histogram, one cell per thread
+
+// Window search, kWindowParts blocks per histogram: the objective at every
+// pair of the candidate cells (each block computes this maximum itself: 256
+// pairs of 16 cells, one per thread), then a flag for each of the block's
+// cells: 2 for a candidate, 1 when its bound reaches the candidates' maximum
+// (less a margin far above the evaluation's error), 0 otherwise; only
+// flagged cells are evaluated. winfo (zeroed by the caller) counts flag 1.
+__global__ void __launch_bounds__(kS2Threads) k_s2_window(const S2Args a) {
+    __shared__ unsigned cand_bits[kCells2d / 32];
+    __shared__ float wbest[kS2Threads / 32];
+    __shared__ int wcount[kS2Threads / 32];
+    const int k = blockIdx.x / kWindowParts, part = blockIdx.x % kWindowParts;
+    const int tid = threadIdx.x, m = a.L2 - 1;
+    for (int i = tid; i < kCells2d / 32; i += kS2Threads) cand_bits[i] = 0u;
+    __syncthreads();
+    float best = -INFINITY;
+    for (int i = tid; i < a.topk * kCell2d * kCell2d; i += kS2Threads) {
+        const int c = a.cand[(long long)k * a.topk + i / (kCell2d * kCell2d)];
+        if (c < 0 || c >= kCells2d) continue;
+        if ((i & (kCell2d * kCell2d - 1)) == 0) atomicOr(&cand_bits[c >> 5], 1u << (c & 31));
+        const int t = (c / 64) * kCell2d + (i & (kCell2d * kCell2d - 1)) / kCell2d;
+        const int s = (c % 64) * kCell2d + (i & (kCell2d - 1));
+        if (t >= m || s >= m) continue;
+        F2 phi;
+        float band;
+        if (eval_df(quad_sums(a, k, t, s), a.q, a.T, phi, band)) best = fmaxf(best, phi.hi + phi.lo);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((tid & 31) == 0) wbest[tid >> 5] = best;
+    __syncthreads();
+    best = wbest[0];
+    for (int w = 1; w < kS2Threads / 32; ++w) best = fmaxf(best, wbest[w]);
+    const float thr = best - 1e-6f * fmaxf(fabsf(best), 1.0f);
+    const int c = part * kS2Threads + tid;
+    const int t0 = (c / 64) * kCell2d, s0 = (c % 64) * kCell2d;
+    unsigned char f = 0;
+    int searched = 0;
+    if ((cand_bits[c >> 5] >> (c & 31)) & 1u) {
+        f = 2;
+    } else if (t0 < m && s0 < m) {
+        const float u = cell_bound(a, k, t0, min(t0 + kCell2d - 1, m - 1), s0, min(s0 + kCell2d - 1, m - 1));
+        if (u >= thr) {
+            f = 1;
+            searched = 1;
+        }
+    }
+    a.cellflag[(long long)k * kCells2d + c] = f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) searched += __shfl_xor_sync(0xffffffffu, searched, o);
+    if ((tid & 31) == 0) wcount[tid >> 5] = searched;
+    __syncthreads();
+    if (tid == 0) {
+        int n = 0;
+        for (int w = 0; w < kS2Threads / 32; ++w) n += wcount[w];
+        if (n) atomicAdd(&a.winfo[k], n);
+    }
+}
+
 __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
     __shared__ TopSmem tsm;
     __shared__ RedSmem sm;
@@ -529,7 +640,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
             a.t_out[2 * k + 1] = g.i % m;
             if (a.t_bin) a.t_bin[k] = g.i / m;
             a.phi_out[k] = g.v.hi + g.v.lo;
-            a.status[k] = TSALLIS_OK;
+            a.status[k] = TSALLIS_OK | window_bits(a, k, g.i / m, g.i % m);
         }
         return;
     }
@@ -578,7 +689,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
         a.t_out[2 * k + 1] = s;
         if (a.t_bin) a.t_bin[k] = t;
         a.phi_out[k] = (float)dv;
-        a.status[k] = TSALLIS_OK | TSALLIS_STATUS_RERANKED;
+        a.status[k] = TSALLIS_OK | TSALLIS_STATUS_RERANKED | window_bits(a, k, t, s);
     }
 }
 
@@ -641,7 +752,8 @@ size_t search2d_scratch_bytes(int L2, long long K) {
     return cells * (2 * sizeof(int) + 2 * sizeof(float2)) + (size_t)K * L2 * 5 * sizeof(float) + 256;
 }
 
-cudaError_t launch_search2d(const Search2dLaunch& p, cudaStream_t s) {
+namespace {
+S2Args s2_args(const Search2dLaunch& p) {
     const int L2 = p.L2;
     const size_t cells = (size_t)p.K * L2 * L2;
     unsigned char* b = static_cast<unsigned char*>(p.scratch);
@@ -665,11 +777,38 @@ cudaError_t launch_search2d(const Search2dLaunch& p, cudaStream_t s) {
     a.t_bin = p.t_bin;
     a.phi_out = p.phi;
     a.status = p.status;
-    k_s2_rows<<<dim3(L2, (unsigned)p.K), kS2Threads, 0, s>>>(a);
-    k_s2_cols<<<dim3((L2 + 31) / 32, (unsigned)p.K), 1024, 0, s>>>(a);
-    k_s2_eval<<<dim3(L2 - 1, (unsigned)p.K), kS2Threads, 0, s>>>(a);
+    a.cand = p.cand;
+    a.topk = p.topk;
+    a.cellflag = p.cellflag;
+    a.winfo = p.winfo;
+    return a;
+}
+}  // namespace
+
+cudaError_t launch_search2d_tables(const Search2dLaunch& p, cudaStream_t s) {
+    const S2Args a = s2_args(p);
+    k_s2_rows<<<dim3(p.L2, (unsigned)p.K), kS2Threads, 0, s>>>(a);
+    k_s2_cols<<<dim3((p.L2 + 31) / 32, (unsigned)p.K), 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_search2d_window(const Search2dLaunch& p, cudaStream_t s) {
+    if (p.L2 != 256 || !p.cand || !p.cellflag || !p.winfo || p.topk < 1) return cudaErrorInvalidValue;
+    if (cudaMemsetAsync(p.winfo, 0, (size_t)p.K * sizeof(int), s) != cudaSuccess) return cudaGetLastError();
+    k_s2_window<<<(unsigned)(p.K * kWindowParts), kS2Threads, 0, s>>>(s2_args(p));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_search2d_finish(const Search2dLaunch& p, cudaStream_t s) {
+    const S2Args a = s2_args(p);
+    k_s2_eval<<<dim3(p.L2 - 1, (unsigned)p.K), kS2Threads, 0, s>>>(a);
     k_s2_final<<<(unsigned)p.K, kS2Threads, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_search2d(const Search2dLaunch& p, cudaStream_t s) {
+    const cudaError_t e = launch_search2d_tables(p, s);
+    return e != cudaSuccess ? e : launch_search2d_finish(p, s);
 }
 
 }  // namespace tsl

@@ -16,6 +16,7 @@ generator. The result is written with tsallis_proposer_save. With
 --resume continues an interrupted run exactly.
 
     python -m paper_2012_10684_gb300.proposer --out weights.bin
+    python -m paper_2012_10684_gb300.proposer --two-d --volumes 300 --steps 6000 --batch 256 --out w2d.bin
 """
 from __future__ import annotations
 
@@ -69,6 +70,45 @@ def make_dataset(n: int, seed: int, dmin: int, dmax: int, q: float = 0.8, nx: in
             print("generated %d volumes, %.1f s" % (i + 1, time.time() - t0), flush=True)
     t, _, st = tg.tsallis_search(hist, p)
     return hist, sub, t, st
+
+
+def make_dataset2d(nvol: int, seed: int, nz: int = 24, q: float = 0.8, nx: int = 512, ny: int = 512,
+                   device="cuda", log_every: int = 0):
+    """(hist [n][256][256], t [n][2], status [n]) for the 2-D search's
+    proposer: from each of nvol generated chest volumes of nz slices, the
+    2-D histogram (256 grey x 256 mean levels) of every slice (3x3 window)
+    and of the volume (3x3x3 window), labelled with the exhaustive 2-D
+    search's pair."""
+    import phantom
+    rng = np.random.default_rng(seed)
+    ps = tg.tsallis_params(q=q, mode="slice", two_d=True)
+    pv = tg.tsallis_params(q=q, mode="volume", two_d=True)
+    per = nz + 1
+    hist = torch.empty((nvol * per, 256, 256), dtype=torch.int32, device=device)
+    buf = torch.empty(nz * ny * nx, dtype=torch.int16, device=device)
+    t0 = time.time()
+    for i in range(nvol):
+        spec = phantom.chest_volume(seed * 100000 + i, nx, ny, nz, generations=int(rng.integers(4, 9)),
+                                    noise_sd=int(rng.integers(5, 31)), vol_id=i)
+        vol = buf.view(nz, ny, nx)
+        phantom.generate_cuda(spec, out=vol)
+        tg.tsallis_histogram(vol, ps, hist[i * per: i * per + nz])
+        tg.tsallis_histogram(vol, pv, hist[i * per + nz: (i + 1) * per])
+        if log_every and (i + 1) % log_every == 0:
+            print("generated %d volumes, %.1f s" % (i + 1, time.time() - t0), flush=True)
+    t, _, st = tg.tsallis_search(hist, ps)
+    return hist, t, st
+
+
+def cell_targets(t: torch.Tensor) -> torch.Tensor:
+    """y [n][4096]: one-hot on the cell 64 * (t // 4) + s // 4 of each pair
+    (rows without a pair stay zero)."""
+    n = t.shape[0]
+    y = torch.zeros((n, 4096), dtype=torch.float32, device=t.device)
+    ok = t[:, 0] >= 0
+    cell = (t[:, 0].long() // 4) * 64 + t[:, 1].long() // 4
+    y[torch.nonzero(ok).squeeze(1), cell[ok]] = 1.0
+    return y
 
 
 def _pack_state(s: int, gen: torch.Generator) -> bytes:
@@ -133,11 +173,29 @@ def main():
     ap.add_argument("--checkpoint", help="training checkpoint written every --checkpoint-every steps")
     ap.add_argument("--checkpoint-every", type=int, default=1000)
     ap.add_argument("--resume", help="checkpoint to continue from (same data arguments)")
+    ap.add_argument("--two-d", action="store_true",
+                    help="train the 2-D search's proposer (slot 1) on per-slice and per-volume 2-D histograms")
+    ap.add_argument("--nz", type=int, default=24, help="slices per generated volume (2-D training)")
     args = ap.parse_args()
     import __graft_entry__
     __graft_entry__.build()
     torch.cuda.set_device(0)
     t0 = time.time()
+    if args.two_d:
+        tg.proposer_select(1)
+        hist, t, st = make_dataset2d(args.volumes, args.seed, nz=args.nz, log_every=50)
+        x = tg.proposer_features(hist)
+        y = cell_targets(t)
+        del hist
+        torch.cuda.synchronize()
+        t1 = time.time()
+        losses = train(x, y, args.steps, args.batch, args.lr, args.seed, log_every=500,
+                       checkpoint=args.checkpoint, checkpoint_every=args.checkpoint_every, resume=args.resume)
+        torch.cuda.synchronize()
+        tg.proposer_save(args.out)
+        print("2-D: %d histograms, data %.1f s, training %.1f s, final loss %.4f" % (
+            x.shape[0], t1 - t0, time.time() - t1, np.nanmean(losses[-100:])))
+        return
     hist, sub, t, st = make_dataset(args.volumes, args.seed, args.dmin, args.dmax, log_every=1000)
     assert bool(((st & 0xff) == 0).all())
     # each volume gives two examples with the same target: its histogram

@@ -106,3 +106,22 @@ def test_pack_unpack_round_trip():
     flat = rng.normal(size=mlp.NPARAM)
     assert np.array_equal(mlp.pack(mlp.unpack(flat)), flat)
     assert mlp.NPARAM == 256 * 256 + 256 + 256 * 256 + 256 + 4096 * 256 + 4096
+
+
+def test_features2d_hand_examples():
+    """Block sums worked by hand: one cell (37, 200) lies in grey block 2 and
+    mean block 12 (feature 44); two cells of block 0 add up; cells in the
+    first and last blocks give log(2)/log(5) and log(4)/log(5)."""
+    h = np.zeros((3, 256, 256), np.int64)
+    h[0, 37, 200] = 9
+    h[1, 0, 0], h[1, 15, 15] = 3, 4
+    h[2, 0, 0], h[2, 255, 255] = 1, 3
+    x = mlp.features2d(h)
+    e0 = np.zeros(256); e0[44] = 1.0
+    assert np.allclose(x[0], e0)
+    e1 = np.zeros(256); e1[0] = 1.0
+    assert np.allclose(x[1], e1)
+    e2 = np.zeros(256); e2[0] = np.log(2) / np.log(5); e2[255] = np.log(4) / np.log(5)
+    assert np.allclose(x[2], e2)
+    assert not mlp.features2d(np.zeros((1, 256, 256))).any()
+    assert mlp.cell2d(37, 200) == 64 * 9 + 50 and mlp.cell2d(254, 254) == 4095
