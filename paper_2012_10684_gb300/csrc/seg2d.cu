@@ -404,6 +404,11 @@ __device__ __forceinline__ double eval64(const Quad& u, float q, const DfTables*
     return (1.0 - ab) / ((double)q - 1.0);
 }
 
+__device__ __forceinline__ bool same_sums(const Quad& x, const Quad& y) {
+    return x.na == y.na && x.nb == y.nb && x.qa.hi == y.qa.hi && x.qa.lo == y.qa.lo && x.qb.hi == y.qb.hi &&
+           x.qb.lo == y.qb.lo;
+}
+
 struct RedSmem {
     float v[kS2Threads / 32];
     float u[kS2Threads / 32];
@@ -648,6 +653,15 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
     auto row_in = [&](int t) {
         return a.ri[ro + t] >= 0 && (a.rvh[ro + t] + a.rband[ro + t] >= lower || a.ru2[ro + t] >= lower);
     };
+    // A pair whose table sums equal its left or upper neighbour's exactly
+    // has that smaller pair's partition and value, so it is neither the
+    // maximiser nor the canonical pair and gets no FP64 evaluation (most
+    // pairs of a plateau; members of one partition whose sums differ in the
+    // last bits, from differently associated scans, are still compared).
+    auto repeats = [&](const Quad& u, int t, int s) {
+        return (s > 0 && same_sums(u, quad_sums(a, k, t, s - 1))) ||
+               (t > 0 && same_sums(u, quad_sums(a, k, t - 1, s)));
+    };
     double dv = 0.0;
     int di = -1;
     for (int t = 0; t < m; ++t) {
@@ -656,7 +670,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
             const Quad u = quad_sums(a, k, t, s);
             F2 phi;
             float band;
-            if (eval_df(u, a.q, a.T, phi, band) && phi.hi + band >= lower)
+            if (eval_df(u, a.q, a.T, phi, band) && phi.hi + band >= lower && !repeats(u, t, s))
                 argmax_merge(dv, di, eval64(u, a.q, a.T), t * m + s);
         }
     }
@@ -678,7 +692,8 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
             if (u.na != uw.na || u.nb != uw.nb) continue;
             F2 phi;
             float band;
-            if (eval_df(u, a.q, a.T, phi, band) && phi.hi + band >= lower && fabs(eval64(u, a.q, a.T) - dv) <= tol)
+            if (eval_df(u, a.q, a.T, phi, band) && phi.hi + band >= lower && !repeats(u, t, s) &&
+                fabs(eval64(u, a.q, a.T) - dv) <= tol)
                 ci = min(ci, t * m + s);
         }
     }
