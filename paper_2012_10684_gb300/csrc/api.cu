@@ -10,6 +10,7 @@
 #include "../../include/tsallis.h"
 #include "../../include/tsallis_testing.h"
 #include "kernels.h"
+#include "preproc_args.h"
 
 using namespace tsl;
 
@@ -1369,18 +1370,20 @@ tsallis_status tsallis_preprocess_params_default(tsallis_preprocess_params* pp) 
 }
 
 namespace {
-// Multiplier and shift with floor(n / d) == (n * m) >> s for every n the
-// level map forms (n <= 511 * D < 2^26): m = floor(2^s / d) + 1 with
-// s = 26 + ceil(log2 d) keeps the error below 1/d; checked exhaustively.
+// Multiplier and shift with floor(n / d) == umulhi(n, m) >> s for every n
+// the level map forms (n <= 511 * D < 2^26, d = 2D): m = floor(2^(32+s) / d)
+// + 1 with s = max(ceil(log2 d) - 2, 0) fits 32 bits and keeps the error
+// below 1/d; checked exhaustively.
 bool level_divider(int D, unsigned long long* m, int* s) {
     const unsigned long long d = 2ull * (unsigned long long)D;
     int l = 0;
     while ((1ull << l) < d) ++l;
-    *s = 26 + l;
-    *m = ((1ull << *s) / d) + 1;
+    *s = l >= 2 ? l - 2 : 0;
+    *m = ((1ull << (32 + *s)) / d) + 1;
+    if (*m > 0xffffffffull) return false;
     for (long long c = 0; c <= D; ++c) {
         const unsigned long long n = (unsigned long long)(2 * c * 255 + D);
-        if (((n * *m) >> *s) != n / d) return false;
+        if ((((n * *m) >> 32) >> *s) != n / d) return false;
     }
     return true;
 }

@@ -223,22 +223,8 @@ cudaError_t launch_search2d_finish(const Search2dLaunch& p, cudaStream_t s);
 size_t search2d_brute_scratch_bytes(int L2, long long K);
 cudaError_t launch_search2d_brute(const Search2dLaunch& p, cudaStream_t s);
 
-// Pre-processing and morphology (preproc.cu): CT numbers to 8-bit levels,
-// flat disk erosion/dilation per slice, chest-mask subtraction, 256-level
-// histograms. Ops follow tsallis_morph_op.
-constexpr int kPreMaxRadius = 15;
-struct PreArgs {
-    const int16_t* vol;     // [nz][ny][nx]
-    int16_t* out;           // [nz][ny][nx] levels 0..255, or null
-    int* hist;              // [nz][256] (per_slice) or [256], zeroed by the caller, or null
-    int nx, ny, nz;
-    int background, hu_min, hu_max;
-    int D;                  // hu_max - hu_min
-    unsigned long long magic;   // floor(n / (2D)) == (n * magic) >> shift for every n the map forms
-    int shift;
-    int op, radius, per_slice;
-    int ntx, nty;           // tiles per slice in x and y
-};
+// Pre-processing and morphology (preproc.cu); arguments in preproc_args.h.
+struct PreArgs;
 int preproc_tile_w();
 int preproc_tile_h();
 cudaError_t preproc_prepare();

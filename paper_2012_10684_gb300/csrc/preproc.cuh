@@ -27,6 +27,7 @@
 #include <cuda_fp16.h>
 
 #include "kernels.h"
+#include "preproc_args.h"
 
 namespace tsl {
 namespace pre {
@@ -109,8 +110,7 @@ __device__ __forceinline__ void disk_run(const uint32_t* src, int stride, int y0
 __device__ __forceinline__ int level_of(int v, const PreArgs& a) {
     if (v <= a.background) return 0;
     const int c = min(max(v, a.hu_min), a.hu_max) - a.hu_min;
-    const unsigned long long n = (unsigned long long)(2 * c * 255 + a.D);
-    return (int)((n * a.magic) >> a.shift);
+    return (int)(__umulhi((unsigned)(2 * c * 255 + a.D), (unsigned)a.magic) >> a.shift);
 }
 
 struct Tile {
@@ -132,31 +132,41 @@ __device__ __forceinline__ void store_mid(uint32_t* mid, int stride, int y, int 
     mid[y * stride + cw] = as_u32(__halves2half2(lo, hi));
 }
 
+// Writes the result for one word (two pixels) of the output tile: the op's
+// value from the morphology result res and the level g, the int16 output
+// (one 4-byte store when both pixels are in and aligned) and the histogram.
 __device__ __forceinline__ void emit(const PreArgs& a, const Tile& t, int y, int cw, __half2 res, uint32_t g,
                                      int& zeros) {
-    const int gy = t.y0 + y;
-    if (gy < 0 || gy >= a.ny) return;
-    const __half2 gg = as_h2(g);
-    const int warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int gx = t.x0 + 2 * cw + e;
-        if (gx < 0 || gx >= a.nx) continue;
-        const int r = __half2int_rn(e ? __high2half(res) : __low2half(res));
-        const int g0 = __half2int_rn(e ? __high2half(gg) : __low2half(gg));
-        int v;
-        switch (a.op) {
-            case kOpChest: v = g0 - r; break;
-            case kOpBlackTop: v = r - g0; break;
-            case kOpCopy: v = g0; break;
-            default: v = r; break;
+    const int gy = t.y0 + y, gx = t.x0 + 2 * cw;
+    if (gy < 0 || gy >= a.ny || gx >= a.nx) return;
+    const float2 rf = __half22float2(res), gf = __half22float2(as_h2(g));
+    float f0, f1;
+    switch (a.op) {
+        case kOpChest: f0 = gf.x - rf.x; f1 = gf.y - rf.y; break;
+        case kOpBlackTop: f0 = rf.x - gf.x; f1 = rf.y - gf.y; break;
+        case kOpCopy: f0 = gf.x; f1 = gf.y; break;
+        default: f0 = rf.x; f1 = rf.y; break;
+    }
+    const int v0 = (int)f0, v1 = (int)f1;      // exact: integers 0..255
+    const bool two = gx + 1 < a.nx;
+    if (a.out) {
+        int16_t* o = a.out + ((long long)t.z * a.ny + gy) * a.nx + gx;
+        if (two && ((uintptr_t)o & 3u) == 0) {
+            *reinterpret_cast<uint32_t*>(o) = (uint32_t)(v0 & 0xffff) | ((uint32_t)v1 << 16);
+        } else {
+            o[0] = (int16_t)v0;
+            if (two) o[1] = (int16_t)v1;
         }
-        if (a.out) a.out[((long long)t.z * a.ny + gy) * a.nx + gx] = (int16_t)v;
-        if (a.hist) {
-            // v is in 0..255 (an opening never exceeds the image, a closing
-            // never falls below it); the clamp only guards the index
-            if (v == 0) ++zeros;
-            else atomicAdd(&t.whist[warp * 256 + min(max(v, 0), 255)], 1);
+    }
+    if (a.hist) {
+        // v is in 0..255 (an opening never exceeds the image, a closing
+        // never falls below it); the clamp only guards the index
+        int* wh = t.whist + (threadIdx.x >> 5) * 256;
+        if (v0 == 0) ++zeros;
+        else atomicAdd(&wh[min(max(v0, 0), 255)], 1);
+        if (two) {
+            if (v1 == 0) ++zeros;
+            else atomicAdd(&wh[min(max(v1, 0), 255)], 1);
         }
     }
 }
@@ -219,31 +229,39 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(PreArgs a) {
     // and turned into levels in place once they have landed; edge pairs and
     // pixels outside the slice are written directly.
     const long long slice0 = (long long)t.z * a.ny * a.nx;
-    const int n_items = gm.rows * gm.stride;
-    for (int i = threadIdx.x; i < n_items; i += kThreads) {
-        const int y = i / gm.stride, cw = i - y * gm.stride;
-        const int gy = t.y0 + y, gx = t.x0 + 2 * cw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int y = warp; y < gm.rows; y += kWarps) {
+        const int gy = t.y0 + y;
         const bool row_in = gy >= 0 && gy < a.ny;
-        const long long e = slice0 + (long long)gy * a.nx + gx;     // element index of the pair
-        if (row_in && gx >= 0 && gx + 1 < a.nx && ((e & 1) == 0)) {
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(&in[i]);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(a.vol + e) : "memory");
-        } else {
-            __half lo = fill, hi = fill;
-            if (row_in && gx >= 0 && gx < a.nx) lo = __int2half_rn(level_of(a.vol[e], a));
-            if (row_in && gx + 1 >= 0 && gx + 1 < a.nx) hi = __int2half_rn(level_of(a.vol[e + 1], a));
-            in[i] = as_u32(__halves2half2(lo, hi));
+        const long long rowe = slice0 + (long long)gy * a.nx;     // element index of (gy, 0)
+        for (int cw = lane; cw < gm.stride; cw += 32) {
+            const int gx = t.x0 + 2 * cw;
+            const long long e = rowe + gx;                        // element index of the pair
+            uint32_t* dst = &in[y * gm.stride + cw];
+            if (row_in && gx >= 0 && gx + 1 < a.nx && ((e & 1) == 0)) {
+                const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(a.vol + e) : "memory");
+            } else {
+                __half lo = fill, hi = fill;
+                if (row_in && gx >= 0 && gx < a.nx) lo = __int2half_rn(level_of(a.vol[e], a));
+                if (row_in && gx + 1 >= 0 && gx + 1 < a.nx) hi = __int2half_rn(level_of(a.vol[e + 1], a));
+                *dst = as_u32(__halves2half2(lo, hi));
+            }
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
-    for (int i = threadIdx.x; i < n_items; i += kThreads) {
-        const int y = i / gm.stride, cw = i - y * gm.stride;
-        const int gy = t.y0 + y, gx = t.x0 + 2 * cw;
-        const long long e = slice0 + (long long)gy * a.nx + gx;
-        if (gy >= 0 && gy < a.ny && gx >= 0 && gx + 1 < a.nx && ((e & 1) == 0)) {
-            const uint32_t raw = in[i];
-            in[i] = as_u32(__halves2half2(__int2half_rn(level_of((int16_t)(raw & 0xffffu), a)),
-                                          __int2half_rn(level_of((int16_t)(raw >> 16), a))));
+    for (int y = warp; y < gm.rows; y += kWarps) {
+        const int gy = t.y0 + y;
+        if (gy < 0 || gy >= a.ny) continue;
+        const long long rowe = slice0 + (long long)gy * a.nx;
+        for (int cw = lane; cw < gm.stride; cw += 32) {
+            const int gx = t.x0 + 2 * cw;
+            if (gx >= 0 && gx + 1 < a.nx && (((rowe + gx) & 1) == 0)) {
+                uint32_t* dst = &in[y * gm.stride + cw];
+                const uint32_t raw = *dst;
+                *dst = as_u32(__halves2half2(__int2half_rn(level_of((int16_t)(raw & 0xffffu), a)),
+                                             __int2half_rn(level_of((int16_t)(raw >> 16), a))));
+            }
         }
     }
     __syncthreads();
