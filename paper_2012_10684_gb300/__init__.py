@@ -350,15 +350,61 @@ def tsallis_segment_batch(vols, p: Params | None = None, masks=None, outs=None):
     return masks, t, phi, st
 
 
-def tsallis_autotune_batch(vols, p: Params | None = None, masks=None, outs=None):
+def autotune_key(vols, p: Params) -> str:
+    """Cache key of a batch's launch shape: the GPU, the parameters that
+    change the work, and the volumes' shapes."""
+    import hashlib
+    dev = vols[0].device
+    props = torch.cuda.get_device_properties(dev)
+    shapes = ",".join("%dx%dx%d" % tuple(int(d) for d in reversed(v.shape[-3:])) for v in vols)
+    return "%s|sm%d|mode%d|2d%d|L%d|shift%d|topk%d|flags%d|%s" % (
+        props.name, props.multi_processor_count, p.mode, p.two_d, p.nbins, p.shift, p.topk, p.flags,
+        hashlib.sha1(shapes.encode()).hexdigest())
+
+
+def autotune_cache_load(path: str) -> dict:
+    """The entries of an autotune cache file ({} when it does not exist)."""
+    import json
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except FileNotFoundError:
+        return {}
+    if not isinstance(d, dict) or d.get("format") != "tsallis-autotune-1":
+        raise ValueError("not an autotune cache: %s" % path)
+    return d.get("entries", {})
+
+
+def autotune_cache_store(path: str, key: str, tile_vox: int, blocks_per_sm: int, best_ms: float) -> None:
+    """Adds (or replaces) one entry; the file is replaced atomically."""
+    import json
+    entries = autotune_cache_load(path)
+    entries[key] = {"tile_vox": int(tile_vox), "blocks_per_sm": int(blocks_per_sm), "best_ms": float(best_ms)}
+    tmp = "%s.tmp%d" % (path, os.getpid())
+    with open(tmp, "w") as f:
+        json.dump({"format": "tsallis-autotune-1", "entries": entries}, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tsallis_autotune_batch(vols, p: Params | None = None, masks=None, outs=None, cache: str | None = None):
     """Times the batch over the launch shapes and keeps the fastest for the
-    context: returns (tile_vox, blocks_per_sm, best_ms)."""
+    context: returns (tile_vox, blocks_per_sm, best_ms). With cache (a JSON
+    file path), a shape found there for this GPU, parameters and volume
+    shapes is applied without timing, and a newly timed one is stored."""
     p = p or tsallis_params()
+    if cache is not None:
+        key = autotune_key(vols, p)
+        hit = autotune_cache_load(cache).get(key)
+        if hit is not None:
+            set_launch_shape(hit["tile_vox"], hit["blocks_per_sm"], vols[0].device)
+            return hit["tile_vox"], hit["blocks_per_sm"], hit["best_ms"]
     vols, masks, arr, t, phi, st = _batch_args(vols, p, masks, outs)
     tv, bps, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
     _check("tsallis_autotune_batch", lib().tsallis_autotune_batch(
         context(vols[0].device), arr, len(vols), ctypes.byref(p), t.data_ptr(), phi.data_ptr(), st.data_ptr(),
         _stream(vols[0]), ctypes.byref(tv), ctypes.byref(bps), ctypes.byref(ms)))
+    if cache is not None:
+        autotune_cache_store(cache, key, tv.value, bps.value, ms.value)
     return tv.value, bps.value, ms.value
 
 

@@ -12,7 +12,22 @@
 #include "kernels.h"
 #include "preproc_args.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace tsl;
+
+namespace {
+// One NVTX range per call of an entry point that enqueues GPU work, named
+// after the entry point, so a trace shows where each call's kernels came
+// from. Without a tool attached the push and pop are no-ops.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+}  // namespace
+#define TSL_TRACE() const TraceRange tsl_trace_range_(__func__)
 
 static_assert(kMlpParams == TSALLIS_PROPOSER_PARAMS, "parameter count of the C ABI");
 
@@ -549,6 +564,7 @@ const char* tsallis_status_string(int32_t status) {
 }
 
 tsallis_status tsallis_create(tsallis_ctx** out, int device) {
+    TSL_TRACE();
     if (!out) return TSALLIS_ERR_INVALID_ARG;
     *out = nullptr;
     int n = 0;
@@ -668,6 +684,7 @@ tsallis_status tsallis_set_speculation(tsallis_ctx* c, int32_t on) {
 
 tsallis_status tsallis_histogram(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
                                  const tsallis_params* p, int32_t* d_hist, cudaStream_t stream) {
+    TSL_TRACE();
     tsallis_status st = check_params(p);
     if (st != TSALLIS_OK) return st;
     if ((st = check_shape(nx, ny, nz)) != TSALLIS_OK) return st;
@@ -702,6 +719,7 @@ tsallis_status tsallis_histogram(tsallis_ctx* c, const int16_t* d_vol, int64_t n
 
 tsallis_status tsallis_search(tsallis_ctx* c, const int32_t* d_hist, int64_t nh, const tsallis_params* p,
                               int32_t* d_t, float* d_phi, int32_t* d_status, float* d_curve, cudaStream_t stream) {
+    TSL_TRACE();
     tsallis_status st = check_params(p);
     if (st != TSALLIS_OK) return st;
     if (nh < 0 || nh > (1ll << 31) - 1) return TSALLIS_ERR_INVALID_ARG;
@@ -728,6 +746,7 @@ tsallis_status tsallis_search(tsallis_ctx* c, const int32_t* d_hist, int64_t nh,
 
 tsallis_status tsallis_binarize(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
                                 const int32_t* d_t, const tsallis_params* p, uint8_t* d_mask, cudaStream_t stream) {
+    TSL_TRACE();
     tsallis_status st = check_params(p);
     if (st != TSALLIS_OK) return st;
     if ((st = check_shape(nx, ny, nz)) != TSALLIS_OK) return st;
@@ -765,6 +784,7 @@ tsallis_status tsallis_binarize(tsallis_ctx* c, const int16_t* d_vol, int64_t nx
 tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
                                const tsallis_params* p, uint8_t* d_mask, int32_t* d_t, float* d_phi,
                                int32_t* d_status, cudaStream_t stream) {
+    TSL_TRACE();
     tsallis_status st = check_params(p);
     if (st != TSALLIS_OK) return st;
     if ((st = check_shape(nx, ny, nz)) != TSALLIS_OK) return st;
@@ -855,6 +875,7 @@ tsallis_status tsallis_probe_dfmath(tsallis_ctx* c, const uint32_t* d_h, int64_t
 tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vols, int32_t nvol,
                                      const tsallis_params* p, int32_t* d_t, float* d_phi, int32_t* d_status,
                                      cudaStream_t stream) {
+    TSL_TRACE();
     tsallis_status st = check_params(p);
     if (st != TSALLIS_OK) return st;
     if (!c || nvol < 0) return TSALLIS_ERR_INVALID_ARG;
@@ -1065,6 +1086,7 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
 }
 
 tsallis_status tsallis_proposer_set(tsallis_ctx* c, const float* h_params, int64_t n) {
+    TSL_TRACE();
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     ProposerSlot& S = c->prop[c->prop_sel];
     if (!h_params || n != kMlpParams) return TSALLIS_ERR_INVALID_ARG;
@@ -1083,6 +1105,7 @@ tsallis_status tsallis_proposer_set(tsallis_ctx* c, const float* h_params, int64
 }
 
 tsallis_status tsallis_proposer_get(tsallis_ctx* c, float* h_params, int64_t n) {
+    TSL_TRACE();
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     ProposerSlot& S = c->prop[c->prop_sel];
     if (!h_params || n != kMlpParams || !S.ready) return TSALLIS_ERR_INVALID_ARG;
@@ -1159,6 +1182,7 @@ struct CkptHeader {
 
 tsallis_status tsallis_proposer_checkpoint_save(tsallis_ctx* c, const char* path, const void* user,
                                                 int64_t user_bytes) {
+    TSL_TRACE();
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     ProposerSlot& S = c->prop[c->prop_sel];
     if (!path || !S.ready || user_bytes < 0 || (user_bytes > 0 && !user)) return TSALLIS_ERR_INVALID_ARG;
@@ -1196,6 +1220,7 @@ tsallis_status tsallis_proposer_checkpoint_save(tsallis_ctx* c, const char* path
 
 tsallis_status tsallis_proposer_checkpoint_load(tsallis_ctx* c, const char* path, void* user, int64_t user_cap,
                                                 int64_t* user_bytes) {
+    TSL_TRACE();
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     ProposerSlot& S = c->prop[c->prop_sel];
     if (!path || user_cap < 0 || (user_cap > 0 && !user)) return TSALLIS_ERR_INVALID_ARG;
@@ -1238,6 +1263,7 @@ tsallis_status tsallis_proposer_checkpoint_load(tsallis_ctx* c, const char* path
 
 tsallis_status tsallis_proposer_features(tsallis_ctx* c, const int32_t* d_hist, int64_t nh, float* d_x,
                                          cudaStream_t stream) {
+    TSL_TRACE();
     if (!c || nh < 0 || (nh > 0 && (!d_hist || !d_x))) return TSALLIS_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
@@ -1253,6 +1279,7 @@ tsallis_status tsallis_proposer_select(tsallis_ctx* c, int32_t slot) {
 
 tsallis_status tsallis_proposer_forward(tsallis_ctx* c, const float* d_x, int32_t B, float* d_logits,
                                         cudaStream_t stream) {
+    TSL_TRACE();
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     ProposerSlot& S = c->prop[c->prop_sel];
     if (B < 0 || (B > 0 && (!d_x || !d_logits)) || !S.ready) return TSALLIS_ERR_INVALID_ARG;
@@ -1270,6 +1297,7 @@ tsallis_status tsallis_proposer_forward(tsallis_ctx* c, const float* d_x, int32_
 
 tsallis_status tsallis_proposer_train_step(tsallis_ctx* c, const float* d_x, const float* d_y, int32_t B, float lr,
                                            int32_t update, float* d_loss, float* d_grad, cudaStream_t stream) {
+    TSL_TRACE();
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     ProposerSlot& S = c->prop[c->prop_sel];
     if (B < 1 || !d_x || !d_y || !d_loss || !S.ready || !(lr >= 0.f)) return TSALLIS_ERR_INVALID_ARG;
@@ -1294,6 +1322,7 @@ tsallis_status tsallis_autotune_batch(tsallis_ctx* c, const tsallis_volume* h_vo
                                       const tsallis_params* p, int32_t* d_t, float* d_phi, int32_t* d_status,
                                       cudaStream_t stream, int32_t* tile_vox, int32_t* blocks_per_sm,
                                       float* best_ms) {
+    TSL_TRACE();
     if (!c) return TSALLIS_ERR_INVALID_ARG;
     tsallis_status st = check_params(p);
     if (st != TSALLIS_OK) return st;
@@ -1392,6 +1421,7 @@ bool level_divider(int D, unsigned long long* m, int* s) {
 tsallis_status tsallis_preprocess(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
                                   const tsallis_preprocess_params* pp, int16_t* d_out, int32_t* d_hist,
                                   cudaStream_t stream) {
+    TSL_TRACE();
     if (!c || !pp) return TSALLIS_ERR_INVALID_ARG;
     if (pp->radius < 0 || pp->radius > kPreMaxRadius || pp->op < TSALLIS_MORPH_NONE ||
         pp->op > TSALLIS_MORPH_BLACK_TOPHAT || (pp->per_slice != 0 && pp->per_slice != 1))

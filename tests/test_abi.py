@@ -98,3 +98,20 @@ def test_python_binding_refuses_cpu_tensors(L):
     v = torch.zeros((2, 4, 4), dtype=torch.int16)
     with pytest.raises(TypeError):
         tg.tsallis_segment(v)
+
+
+def test_autotune_cache_file_round_trip(tmp_path):
+    """The cache file format (no GPU): entries are added and replaced, the
+    file is JSON with a format tag, and a foreign file is refused."""
+    path = str(tmp_path / "tune.json")
+    assert tg.autotune_cache_load(path) == {}
+    tg.autotune_cache_store(path, "gpu|a", 65536, 2, 1.5)
+    tg.autotune_cache_store(path, "gpu|b", 32768, 1, 2.5)
+    tg.autotune_cache_store(path, "gpu|a", 131072, 2, 1.25)
+    e = tg.autotune_cache_load(path)
+    assert e == {"gpu|a": {"tile_vox": 131072, "blocks_per_sm": 2, "best_ms": 1.25},
+                 "gpu|b": {"tile_vox": 32768, "blocks_per_sm": 1, "best_ms": 2.5}}
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"something": 1}')
+    with pytest.raises(ValueError):
+        tg.autotune_cache_load(str(bad))

@@ -142,6 +142,29 @@ def test_batch_autotune_picks_a_valid_shape_and_keeps_results():
     _check_batch(vols_np, "volume", 0.8)
 
 
+def test_batch_autotune_cache(tmp_path):
+    """The first call times the shapes and stores the winner; the second
+    finds it for the same GPU, parameters and shapes and applies it without
+    timing; other shapes miss."""
+    vols_np = _uneven(19, 3, 256, 256, 8, 20)
+    vols = [torch.from_numpy(v).cuda() for v in vols_np]
+    p = tg.tsallis_params(q=0.8, mode="volume")
+    cache = str(tmp_path / "tune.json")
+    try:
+        first = tg.tsallis_autotune_batch(vols, p, cache=cache)
+        entries = tg.autotune_cache_load(cache)
+        assert len(entries) == 1 and list(entries.values())[0]["tile_vox"] == first[0]
+        tg.set_launch_shape(65536, 0)
+        import time
+        t0 = time.time()
+        second = tg.tsallis_autotune_batch(vols, p, cache=cache)
+        assert second == first and time.time() - t0 < 0.5
+        tg.tsallis_autotune_batch(vols[:2], p, cache=cache)
+        assert len(tg.autotune_cache_load(cache)) == 2
+    finally:
+        tg.set_launch_shape(65536, 0)
+
+
 def test_batch_argument_errors():
     L = tg.lib()
     ctx = tg.context()
