@@ -25,6 +25,19 @@ extern "C" {
 tsallis_status tsallis_probe_dfmath(tsallis_ctx* ctx, const uint32_t* d_h, int64_t n, uint32_t N, float q,
                                    double* d_pow, double* d_log2, cudaStream_t stream);
 
+/*
+ * Checked build only (the library compiled with -DTSALLIS_CHECKED): the
+ * kernels test the indices they compute against the extents of the buffers
+ * they address, skip an access that fails and record the first failing
+ * site. This call waits for the device, writes that site number to *site (0:
+ * every check passed since the last call) and clears it. In normal builds it
+ * returns TSALLIS_ERR_UNIMPLEMENTED. Site numbers: 101-103 the tile kernel
+ * (group, tile, binarise queue), 201-206 pre-processing (staged word, voxel
+ * read, disk window, intermediate word, output voxel, histogram level),
+ * 301-303 the 2-D search (table entries, candidate cell, brute-force row).
+ */
+tsallis_status tsallis_check_status(tsallis_ctx* ctx, uint32_t* site);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,12 +115,15 @@ _SIGS = {
                                     ctypes.c_int),
     "tsallis_preprocess_params_default": ([ctypes.POINTER(PreprocessParams)], ctypes.c_int),
     "tsallis_preprocess": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(PreprocessParams), _P, _P, _P], ctypes.c_int),
+    "tsallis_check_status": ([_P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "tsallis_probe_dfmath": ([_P, _P, _I64, ctypes.c_uint32, ctypes.c_float, _P, _P, _P], ctypes.c_int),
 }
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the checked build when the
+    environment sets TSALLIS_CHECKED=1, else the normal one."""
+    return _build.LIB_CHECKED if os.environ.get("TSALLIS_CHECKED") == "1" else _build.LIB
 
 
 def lib():
@@ -128,10 +131,10 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(_build.LIB):
+            if not os.path.exists(library_path()):
                 raise RuntimeError("libtsallis.so is not built (run paper_2012_10684_gb300.build.build()); "
                                    "there is no CPU fallback")
-            L = ctypes.CDLL(_build.LIB)
+            L = ctypes.CDLL(library_path())
             for name, (args, res) in _SIGS.items():
                 f = getattr(L, name)
                 f.argtypes = args
@@ -524,3 +527,11 @@ def proposer_select(slot: int, device=None) -> None:
     dev = torch.cuda.current_device() if device is None else torch.device(device).index
     _check("tsallis_proposer_select", lib().tsallis_proposer_select(context(dev), int(slot)))
     _selected[dev] = int(slot)
+
+
+def check_status(device=None) -> int:
+    """Checked build: the first failing index check's site since the last
+    call (0: none); raises in a normal build."""
+    v = ctypes.c_uint32(0)
+    _check("tsallis_check_status", lib().tsallis_check_status(context(device), ctypes.byref(v)))
+    return v.value

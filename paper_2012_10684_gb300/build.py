@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtsallis.so")
+# the checked build (-DTSALLIS_CHECKED: index checks in the kernels) lives apart
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libtsallis.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", "-I", INCLUDE] + ARCH
@@ -41,19 +44,23 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    """Compile every CUDA source of the library and link libtsallis.so."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, ptxas_verbose: bool = False, checked: bool = False) -> str:
+    """Compile every CUDA source of the library and link libtsallis.so (with
+    checked=True the checked build, into its own directory)."""
+    out_dir = BUILD_CHECKED if checked else BUILD
+    lib_path = LIB_CHECKED if checked else LIB
+    flags = NVCC_FLAGS + (["-DTSALLIS_CHECKED"] if checked else [])
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdrs = _headers()
     nvcc = _nvcc()
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(out_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if _stale(o, [s] + hdrs) or ptxas_verbose:
-            cmd = [nvcc] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_verbose else []) + ["-c", s, "-o", o]
+            cmd = [nvcc] + flags + (["-Xptxas", "-v"] if ptxas_verbose else []) + ["-c", s, "-o", o]
             jobs.append(cmd)
 
     def run(cmd):
@@ -67,14 +74,14 @@ def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
                     raise RuntimeError("nvcc failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
                 if verbose or ptxas_verbose:
                     sys.stdout.write(r.stdout + r.stderr)
-    if _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    if _stale(lib_path, objs):
+        tmp = lib_path + ".tmp"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -9,6 +9,7 @@
 
 #include "../../include/tsallis.h"
 #include "../../include/tsallis_testing.h"
+#include "checked.cuh"
 #include "kernels.h"
 #include "preproc_args.h"
 
@@ -86,6 +87,7 @@ struct tsallis_ctx {
     // predicted thresholds and the search's other outputs
     void* pred_buf = nullptr;
     int pred_cap = 0;
+    unsigned* check = nullptr;    // checked build: first failing index check (checked.cuh)
 };
 
 namespace {
@@ -427,6 +429,7 @@ cudaError_t search2d_enqueue(tsallis_ctx* c, void* scratch, const int32_t* d_his
     }
     for (long long k0 = 0; k0 < nh; k0 += kSearch2dChunk) {
         Search2dLaunch s{};
+        s.check = c->check;
         s.K = nh - k0 < kSearch2dChunk ? nh - k0 : kSearch2dChunk;
         s.hist = d_hist + k0 * cells;
         s.L2 = L2;
@@ -480,6 +483,7 @@ void fill_common(SegArgs& a, const tsallis_params* p, tsallis_ctx* c) {
     a.timeout_ns = c->timeout_ns;
     a.tile_vox = c->tile_vox;
     a.df_tables = c->df_tables;
+    a.check = c->check;
 }
 
 tsallis_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TSALLIS_OK : TSALLIS_ERR_CUDA; }
@@ -628,6 +632,12 @@ tsallis_status tsallis_create(tsallis_ctx** out, int device) {
         delete c;
         return TSALLIS_ERR_CUDA;
     }
+    if (cudaMalloc(&c->check, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(c->check, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        tsallis_destroy(c);
+        return TSALLIS_ERR_CUDA;
+    }
     *out = c;
     return TSALLIS_OK;
 }
@@ -648,6 +658,7 @@ void tsallis_destroy(tsallis_ctx* c) {
         }
         if (c->prop_x) cudaFree(c->prop_x);
         if (c->pred_buf) cudaFree(c->pred_buf);
+        if (c->check) cudaFree(c->check);
     }
     delete c;
 }
@@ -1467,5 +1478,22 @@ tsallis_status tsallis_preprocess(tsallis_ctx* c, const int16_t* d_vol, int64_t 
     a.per_slice = pp->per_slice;
     a.ntx = (int)ntx;
     a.nty = (int)nty;
+    a.check = c->check;
     return cuda_status(launch_preprocess(a, stream));
+}
+
+// ------------------------------------------------------------ checked build
+
+tsallis_status tsallis_check_status(tsallis_ctx* c, uint32_t* site) {
+    if (!c || !site) return TSALLIS_ERR_INVALID_ARG;
+    if (!kCheckedBuild) return TSALLIS_ERR_UNIMPLEMENTED;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    unsigned v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&v, c->check, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(c->check, 0, sizeof(unsigned)) != cudaSuccess)
+        return TSALLIS_ERR_CUDA;
+    *site = v;
+    return TSALLIS_OK;
 }

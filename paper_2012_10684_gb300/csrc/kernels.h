@@ -79,6 +79,7 @@ struct SegArgs {
     const void* df_tables;  // double-float log2/exp2 tables (device)
     const float2* ptab;     // optional: terms 2^64 (n / ptab_n)^q (q = 1: n log2 n) for n = 0..ptab_n;
     long long ptab_n;       // groups of exactly ptab_n voxels are searched with it
+    unsigned* check;        // checked build: first failing index check (checked.cuh)
 };
 
 // A volume of a batch as the descriptor-expansion kernel receives it: its
@@ -208,6 +209,7 @@ struct Search2dLaunch {
     int topk;
     unsigned char* cellflag;
     int* winfo;
+    unsigned* check;        // checked build: first failing index check (checked.cuh)
 };
 cudaError_t seg2d_prepare();
 cudaError_t hist2d_occupancy(int* blocks_per_sm);

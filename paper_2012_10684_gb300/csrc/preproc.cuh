@@ -26,6 +26,7 @@
 #pragma once
 #include <cuda_fp16.h>
 
+#include "checked.cuh"
 #include "kernels.h"
 #include "preproc_args.h"
 
@@ -116,6 +117,8 @@ __device__ __forceinline__ int level_of(int v, const PreArgs& a) {
 struct Tile {
     int z, x0, y0;          // image pixel of shared word column 0 / row 0
     int* whist;             // [kWarps][256]
+    int rows, stride;       // shared tile geometry (words), for the checked build
+    long long total;        // voxels of the volume, for the checked build
 };
 
 // Stores pass-0 results into the intermediate image, with pixels outside
@@ -129,7 +132,8 @@ __device__ __forceinline__ void store_mid(uint32_t* mid, int stride, int y, int 
     __half lo = __low2half(v), hi = __high2half(v);
     if (!row_in || gx < 0 || gx >= a.nx) lo = n;
     if (!row_in || gx + 1 < 0 || gx + 1 >= a.nx) hi = n;
-    mid[y * stride + cw] = as_u32(__halves2half2(lo, hi));
+    if (in_range((long long)y * stride + cw, (long long)t.rows * t.stride, a.check, kSitePreMid))
+        mid[y * stride + cw] = as_u32(__halves2half2(lo, hi));
 }
 
 // Writes the result for one word (two pixels) of the output tile: the op's
@@ -149,7 +153,7 @@ __device__ __forceinline__ void emit(const PreArgs& a, const Tile& t, int y, int
     }
     const int v0 = (int)f0, v1 = (int)f1;      // exact: integers 0..255
     const bool two = gx + 1 < a.nx;
-    if (a.out) {
+    if (a.out && in_range(((long long)t.z * a.ny + gy) * a.nx + gx + (two ? 1 : 0), t.total, a.check, kSitePreOut)) {
         int16_t* o = a.out + ((long long)t.z * a.ny + gy) * a.nx + gx;
         if (two && ((uintptr_t)o & 3u) == 0) {
             *reinterpret_cast<uint32_t*>(o) = (uint32_t)(v0 & 0xffff) | ((uint32_t)v1 << 16);
@@ -163,12 +167,20 @@ __device__ __forceinline__ void emit(const PreArgs& a, const Tile& t, int y, int
         // never falls below it); the clamp only guards the index
         int* wh = t.whist + (threadIdx.x >> 5) * 256;
         if (v0 == 0) ++zeros;
-        else atomicAdd(&wh[min(max(v0, 0), 255)], 1);
+        else if (in_range(v0, 256, a.check, kSitePreHist)) atomicAdd(&wh[min(max(v0, 0), 255)], 1);
         if (two) {
             if (v1 == 0) ++zeros;
-            else atomicAdd(&wh[min(max(v1, 0), 255)], 1);
+            else if (in_range(v1, 256, a.check, kSitePreHist)) atomicAdd(&wh[min(max(v1, 0), 255)], 1);
         }
     }
+}
+
+// Checked build: the rows and words a disk run reads lie inside the tile.
+template <int R, int K>
+__device__ __forceinline__ bool window_ok(int y0, int cw, const Tile& t, const PreArgs& a) {
+    constexpr int P = pad_words(R);
+    return in_range(y0 - R, t.rows, a.check, kSitePreWindow) && in_range(y0 + K - 1 + R, t.rows, a.check, kSitePreWindow) &&
+           in_range(cw - P, t.stride, a.check, kSitePreWindow) && in_range(cw + P, t.stride, a.check, kSitePreWindow);
 }
 
 template <int R, int K, bool kMax>
@@ -178,6 +190,7 @@ __device__ __forceinline__ void final_pass(const uint32_t* src, const uint32_t* 
     for (int it = threadIdx.x; it < kTWw * kChunks; it += kThreads) {
         const int cw = cw0 + it % kTWw;
         const int y0 = row0 + (it / kTWw) * K;
+        if (kCheckedBuild && !window_ok<R, K>(y0, cw, t, a)) continue;
         __half2 acc[K];
         disk_run<R, K, kMax>(src, stride, y0, cw, acc);
 #pragma unroll
@@ -194,6 +207,7 @@ __device__ __forceinline__ void first_of_two(const uint32_t* in, uint32_t* mid, 
     for (int it = threadIdx.x; it < ncw * kChunks; it += kThreads) {
         const int cw = P + it % ncw;
         const int y0 = R + (it / ncw) * K;
+        if (kCheckedBuild && !window_ok<R, K>(y0, cw, t, a)) continue;
         __half2 acc[K];
         disk_run<R, K, kMax>(in, stride, y0, cw, acc);
 #pragma unroll
@@ -218,6 +232,9 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(PreArgs a) {
     t.x0 = tx * kTW - np * 2 * pad_words(R);
     t.y0 = ty * kTH - np * R;
     t.whist = whist;
+    t.rows = gm.rows;
+    t.stride = gm.stride;
+    t.total = (long long)a.nz * a.ny * a.nx;
 
     if (a.hist)
         for (int i = threadIdx.x; i < kWarps * 256; i += kThreads) whist[i] = 0;
@@ -238,6 +255,11 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(PreArgs a) {
             const int gx = t.x0 + 2 * cw;
             const long long e = rowe + gx;                        // element index of the pair
             uint32_t* dst = &in[y * gm.stride + cw];
+            if (kCheckedBuild && row_in && gx >= 0 && gx < a.nx &&
+                !in_range(e + (gx + 1 < a.nx ? 1 : 0), t.total, a.check, kSitePreVol)) {
+                *dst = 0u;
+                continue;
+            }
             if (row_in && gx >= 0 && gx + 1 < a.nx && ((e & 1) == 0)) {
                 const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
                 asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(a.vol + e) : "memory");

@@ -18,6 +18,7 @@ struct PreArgs {
     int shift;
     int op, radius, per_slice;
     int ntx, nty;           // tiles per slice in x and y
+    unsigned* check;        // checked build: first failing index check (checked.cuh)
 };
 
 }  // namespace tsl

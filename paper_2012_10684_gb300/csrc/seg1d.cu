@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "dfmath.cuh"
 #include "search1d.cuh"
+#include "checked.cuh"
 #include "kernels.h"
 
 namespace tsl {
@@ -480,6 +481,12 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
             handoff_sync();
             Work w = s_work[i & 1];
             if (w.kind == 0) break;
+            // checked build: an item outside the groups or its group's tiles
+            // is skipped by every worker (w is the same for the whole block)
+            if (kCheckedBuild && (!in_range(w.group, a.ngroups, a.check, kSiteSegGroup) ||
+                                  (!(w.kind == 2 && (w.tile & kPatchItem)) &&
+                                   !in_range(w.tile, group_tiles(a, w.group), a.check, kSiteSegTile))))
+                continue;
             const int16_t* gvol;
             uint8_t* gmask;
             long long gn;
@@ -632,6 +639,7 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                         // all work is done)
                         const int base = s_last;
                         for (int j = tid; j < nt; j += kSegThreads)
+                            if (in_range(base + j, a.ntotal, a.check, kSiteSegQueue))
                             st_release_u64(&a.bq[base + j],
                                            bq_pack(epoch, w.group,
                                                    patch ? (kPatchItem | j) : exact ? kNoopTile : nt - 1 - j));

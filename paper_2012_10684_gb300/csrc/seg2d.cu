@@ -36,6 +36,7 @@
 //               the same value the smallest (t, s) is returned.
 #include <cmath>
 
+#include "checked.cuh"
 #include "common.cuh"
 #include "dfmath.cuh"
 #include "kernels.h"
@@ -246,6 +247,8 @@ struct S2Args {
     int topk;
     unsigned char* cellflag;   // [K][kCells2d]
     int* winfo;           // [K] cells searched beyond the candidates
+    long long K;          // histograms
+    unsigned* check;      // checked build: first failing index check
 };
 
 __device__ __forceinline__ long long s2_off(const S2Args& a, int k) { return (long long)k * a.L2 * a.L2; }
@@ -386,6 +389,9 @@ struct Quad {
 __device__ __forceinline__ Quad quad_sums(const S2Args& a, int k, int t, int s) {
     const long long o = s2_off(a, k);
     const long long ea = o + (long long)t * a.L2 + s, eb = o + (long long)(t + 1) * a.L2 + (s + 1);
+    const long long cells = a.K * a.L2 * a.L2;
+    if (kCheckedBuild && !(in_range(ea, cells, a.check, kSite2dTables) && in_range(eb, cells, a.check, kSite2dTables)))
+        return Quad{0, 0, F2{0.f, 0.f}, F2{0.f, 0.f}};
     const float2 x = a.PW[ea], y = a.SW[eb];
     return Quad{a.PC[ea], a.SC[eb], F2{x.x, x.y}, F2{y.x, y.y}};
 }
@@ -577,7 +583,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_window(const S2Args a) {
     float best = -INFINITY;
     for (int i = tid; i < a.topk * kCell2d * kCell2d; i += kS2Threads) {
         const int c = a.cand[(long long)k * a.topk + i / (kCell2d * kCell2d)];
-        if (c < 0 || c >= kCells2d) continue;
+        if (!in_range(c, kCells2d, a.check, kSite2dCell) || c < 0 || c >= kCells2d) continue;
         if ((i & (kCell2d * kCell2d - 1)) == 0) atomicOr(&cand_bits[c >> 5], 1u << (c & 31));
         const int t = (c / 64) * kCell2d + (i & (kCell2d * kCell2d - 1)) / kCell2d;
         const int s = (c % 64) * kCell2d + (i & (kCell2d - 1));
@@ -796,6 +802,8 @@ S2Args s2_args(const Search2dLaunch& p) {
     a.topk = p.topk;
     a.cellflag = p.cellflag;
     a.winfo = p.winfo;
+    a.K = p.K;
+    a.check = p.check;
     return a;
 }
 }  // namespace

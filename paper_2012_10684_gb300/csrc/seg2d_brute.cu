@@ -18,6 +18,7 @@
 // the best t (smallest t among equal values): the smallest (t, s) overall.
 #include <math.h>
 
+#include "checked.cuh"
 #include "kernels.h"
 #include "tsallis.h"
 
@@ -38,6 +39,8 @@ struct BruteArgs {
     int* t_bin;             // optional [K]
     float* phi_out;
     int* status;
+    long long K;
+    unsigned* check;        // checked build: first failing index check
 };
 
 __global__ void k_brute_terms(const int* hist, long long n, float q, float* T) {
@@ -70,9 +73,10 @@ __global__ void __launch_bounds__(kBruteThreads) k_brute_pairs(const BruteArgs a
     float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
     for (int i = 0; i < L2; ++i) {
         __syncthreads();
+        const bool row_ok = in_range(base + (long long)i * L2 + L2 - 1, a.K * L2 * L2, a.check, kSite2dBrute);
         for (int j = threadIdx.x; j < L2; j += kBruteThreads) {
-            sT[j] = a.T[base + (long long)i * L2 + j];
-            sH[j] = a.hist[base + (long long)i * L2 + j];
+            sT[j] = row_ok ? a.T[base + (long long)i * L2 + j] : 0.f;
+            sH[j] = row_ok ? a.hist[base + (long long)i * L2 + j] : 0;
         }
         __syncthreads();
         if (s < m) {
@@ -206,6 +210,8 @@ cudaError_t launch_search2d_brute(const Search2dLaunch& p, cudaStream_t s) {
     a.t_bin = p.t_bin;
     a.phi_out = p.phi;
     a.status = p.status;
+    a.K = p.K;
+    a.check = p.check;
     const long long n = p.K * L2 * L2;
     k_brute_terms<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.hist, n, p.q, T);
     dim3 grid((unsigned)(L2 - 1), (unsigned)p.K);
