@@ -26,6 +26,15 @@ tsallis_status tsallis_probe_dfmath(tsallis_ctx* ctx, const uint32_t* d_h, int64
                                    double* d_pow, double* d_log2, cudaStream_t stream);
 
 /*
+ * The proposer's top-k selection on caller data: for each of the B rows of
+ * d_logits [B][4096] (device, float), the indices of its k largest values in
+ * descending order, equal values ranked by the smaller index, into d_out
+ * [B][k] (device). 1 <= k <= 256. Errors: TSALLIS_ERR_INVALID_ARG.
+ */
+tsallis_status tsallis_probe_topk(tsallis_ctx* ctx, const float* d_logits, int32_t B, int32_t k, int32_t* d_out,
+                                  cudaStream_t stream);
+
+/*
  * Checked build only (the library compiled with -DTSALLIS_CHECKED): the
  * kernels test the indices they compute against the extents of the buffers
  * they address, skip an access that fails and record the first failing

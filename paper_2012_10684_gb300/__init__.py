@@ -116,6 +116,7 @@ _SIGS = {
     "tsallis_preprocess_params_default": ([ctypes.POINTER(PreprocessParams)], ctypes.c_int),
     "tsallis_preprocess": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(PreprocessParams), _P, _P, _P], ctypes.c_int),
     "tsallis_check_status": ([_P, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "tsallis_probe_topk": ([_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
     "tsallis_probe_dfmath": ([_P, _P, _I64, ctypes.c_uint32, ctypes.c_float, _P, _P, _P], ctypes.c_int),
 }
 
@@ -535,3 +536,14 @@ def check_status(device=None) -> int:
     v = ctypes.c_uint32(0)
     _check("tsallis_check_status", lib().tsallis_check_status(context(device), ctypes.byref(v)))
     return v.value
+
+
+def probe_topk(z: torch.Tensor, k: int) -> torch.Tensor:
+    """Test hook: the proposer's top-k indices [B][k] of logits [B][4096]."""
+    if not z.is_cuda or z.dtype != torch.float32 or not z.is_contiguous() or z.shape[-1] != 4096:
+        raise TypeError("logits must be a contiguous float32 CUDA tensor [B][4096]")
+    B = z.numel() // 4096
+    out = torch.empty((B, k), dtype=torch.int32, device=z.device)
+    _check("tsallis_probe_topk", lib().tsallis_probe_topk(context(z.device), z.data_ptr(), B, int(k), out.data_ptr(),
+                                                          _stream(z)))
+    return out

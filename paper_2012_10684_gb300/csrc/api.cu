@@ -1497,3 +1497,11 @@ tsallis_status tsallis_check_status(tsallis_ctx* c, uint32_t* site) {
     *site = v;
     return TSALLIS_OK;
 }
+
+tsallis_status tsallis_probe_topk(tsallis_ctx* c, const float* d_logits, int32_t B, int32_t k, int32_t* d_out,
+                                  cudaStream_t stream) {
+    if (!c || B < 0 || k < 1 || k > 256 || (B > 0 && (!d_logits || !d_out))) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    return cuda_status(mlp_topk(d_logits, B, k, d_out, stream));
+}

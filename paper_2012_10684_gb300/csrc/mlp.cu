@@ -119,6 +119,137 @@ cudaError_t gemm(int M, int N, int K, const float* A, int lda, const __nv_bfloat
     return cudaGetLastError();
 }
 
+// Forward layers for small batches (the searches' proposals: a few to 64
+// rows per launch): C[m][n] = act(sum_k X[m][k] W[n][k] + bias[n]) with
+// K = 256. A block owns 16 outputs of up to 64 rows; thread (m, g) computes
+// outputs n0 + 4g .. n0 + 4g + 3 of row m. The rows' inputs are staged in
+// shared memory 64 columns at a time with a padded stride (the 32 lanes of a
+// warp read 32 rows of one column: distinct banks); the 16 weight rows are
+// read as broadcasts. Epilogue as k_gemm's kEpi 1 (bias) and 2 (bias, Z,
+// GELU).
+constexpr int kSmallRows = 64, kSmallCols = 16, kSmallK = 64;
+template <int kEpi>
+__global__ void __launch_bounds__(256) k_gemm_small(int M, int N, const float* __restrict__ X,
+                                                  const __nv_bfloat16* __restrict__ W,
+                                                  const float* __restrict__ bias, float* __restrict__ C,
+                                                  float* __restrict__ Z) {
+    __shared__ float xs[kSmallRows][kSmallK + 1];
+    __shared__ float ws[kSmallCols][kSmallK];
+    const int m_local = threadIdx.x & (kSmallRows - 1), g = threadIdx.x >> 6;
+    const int m0 = blockIdx.y * kSmallRows, n0 = blockIdx.x * kSmallCols;
+    const int m = m0 + m_local;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < kMlpIn; k0 += kSmallK) {
+        for (int e = threadIdx.x; e < kSmallRows * kSmallK; e += 256) {
+            const int r = e / kSmallK, kk = e % kSmallK;
+            xs[r][kk] = (m0 + r < M) ? X[(long long)(m0 + r) * kMlpIn + k0 + kk] : 0.f;
+        }
+        for (int e = threadIdx.x; e < kSmallCols * kSmallK; e += 256) {
+            const int c = e / kSmallK, kk = e % kSmallK;
+            ws[c][kk] = (n0 + c < N) ? __bfloat162float(W[(long long)(n0 + c) * kMlpIn + k0 + kk]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kSmallK; ++kk) {
+            const float xv = xs[m_local][kk];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j] = fmaf(xv, ws[g * 4 + j][kk], acc[j]);
+        }
+        __syncthreads();
+    }
+    if (m >= M) return;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int n = n0 + g * 4 + j;
+        if (n >= N) continue;
+        const long long o = (long long)m * N + n;
+        float v = acc[j] + bias[n];
+        if (kEpi == 2) {
+            Z[o] = v;
+            v = gelu_f(v);
+        }
+        C[o] = v;
+    }
+}
+
+template <int kEpi>
+cudaError_t gemm_small(int M, int N, const float* X, const __nv_bfloat16* W, const float* bias, float* C, float* Z,
+                       cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    dim3 grid((N + kSmallCols - 1) / kSmallCols, (M + kSmallRows - 1) / kSmallRows);
+    k_gemm_small<kEpi><<<grid, 256, 0, s>>>(M, N, X, W, bias, C, Z);
+    return cudaGetLastError();
+}
+
+// Top k (k <= 64) of one row of 4096 logits per block, as warp argmax
+// rounds: each of the 16 warps takes the k largest of its 256 keys (a lane
+// holds 8; each round the warp's maximum is found by shuffles and its lane
+// moves to its next key), then warp 0 takes the k largest of the 16 k
+// candidates the same way. Keys are the order-preserving bits of the logit
+// above the complemented index, so equal logits rank the smaller index
+// first; the output is in descending order, as the bitonic kernel's.
+constexpr int kTopkSmallMax = 64;
+__device__ __forceinline__ unsigned long long topk_key(float v, int i) {
+    unsigned u = __float_as_uint(v);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)u << 32) | (unsigned)(0xffffffffu - (unsigned)i);
+}
+template <int kPer>
+__device__ __forceinline__ void warp_topk_rounds(unsigned long long (&key)[kPer], int k, unsigned long long* out) {
+    const int lane = threadIdx.x & 31;
+    // each lane's keys in descending order, so its next key is key[pos]
+#pragma unroll
+    for (int i = 1; i < kPer; ++i)
+#pragma unroll
+        for (int j = i; j > 0; --j)
+            if (key[j] > key[j - 1]) {
+                const unsigned long long t = key[j];
+                key[j] = key[j - 1];
+                key[j - 1] = t;
+            }
+    int pos = 0;
+    for (int r = 0; r < k; ++r) {
+        unsigned long long head = 0ull;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+            if (i == pos) head = key[i];
+        unsigned long long best = head;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other > best ? other : best;
+        }
+        if (head == best && head != 0ull) ++pos;   // keys are distinct: one lane owns the maximum
+        if (lane == 0) out[r] = best;
+    }
+}
+__global__ void __launch_bounds__(512) k_topk_small(const float* __restrict__ z, int k, int32_t* __restrict__ out) {
+    __shared__ unsigned long long cand[16][kTopkSmallMax];
+    const int row = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float* zr = z + (long long)row * kMlpOut;
+    unsigned long long key[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int i = warp * 256 + j * 32 + lane;
+        key[j] = topk_key(zr[i], i);
+    }
+    warp_topk_rounds<8>(key, k, cand[warp]);
+    __syncthreads();
+    if (warp != 0) return;
+    // warp 0: lane l holds candidates l, l + 32, ... of the 16 k (at most 32 per lane)
+    unsigned long long key2[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int c = j * 32 + lane;
+        key2[j] = c < 16 * k ? cand[c / k][c % k] : 0ull;
+    }
+    __shared__ unsigned long long fin[kTopkSmallMax];
+    warp_topk_rounds<32>(key2, k, fin);
+    __syncwarp();
+    for (int r = lane; r < k; r += 32)
+        out[(long long)row * k + r] = (int32_t)(0xffffffffu - (unsigned)(fin[r] & 0xffffffffu));
+}
+
 // x[h][k] = log1p(sum of levels 16k..16k+15) / log1p(N); one block per histogram.
 __global__ void __launch_bounds__(kMlpIn) k_features(const int32_t* __restrict__ hist, long long nh,
                                                        float* __restrict__ x) {
@@ -302,6 +433,11 @@ cudaError_t mlp_to_bf16(const float* p, void* p16, long long n, cudaStream_t s) 
 cudaError_t mlp_forward(const MlpBuffers& b, const float* x, int B, cudaStream_t s) {
     const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(b.p16);
     cudaError_t e;
+    if (B <= kSmallRows) {
+        if ((e = gemm_small<2>(B, kMlpHid, x, w + kOffW1, b.p32 + kOffB1, b.a1, b.z1, s)) != cudaSuccess) return e;
+        if ((e = gemm_small<2>(B, kMlpHid, b.a1, w + kOffW2, b.p32 + kOffB2, b.a2, b.z2, s)) != cudaSuccess) return e;
+        return gemm_small<1>(B, kMlpOut, b.a2, w + kOffW3, b.p32 + kOffB3, b.z3, nullptr, s);
+    }
     if ((e = gemm<0, 0, 2>(B, kMlpHid, kMlpIn, x, kMlpIn, w + kOffW1, nullptr, kMlpIn, b.p32 + kOffB1, b.a1, b.z1,
                            kMlpHid, s)) != cudaSuccess) return e;
     if ((e = gemm<0, 0, 2>(B, kMlpHid, kMlpHid, b.a1, kMlpHid, w + kOffW2, nullptr, kMlpHid, b.p32 + kOffB2, b.a2,
@@ -349,7 +485,8 @@ cudaError_t mlp_adam(const MlpBuffers& b, float lr, int step, cudaStream_t s) {
 
 cudaError_t mlp_topk(const float* z, int B, int k, int32_t* out, cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
-    k_topk<<<B, 512, 0, s>>>(z, k, out);
+    if (k >= 1 && k <= kTopkSmallMax) k_topk_small<<<B, 512, 0, s>>>(z, k, out);
+    else k_topk<<<B, 512, 0, s>>>(z, k, out);
     return cudaGetLastError();
 }
 

@@ -116,6 +116,23 @@ def test_adam_step_matches_oracle():
     assert np.allclose(p1, po, rtol=1e-5, atol=1e-7)
 
 
+@pytest.mark.parametrize("k", [1, 2, 16, 64, 65, 256])
+def test_topk_matches_a_sort(k):
+    """Both top-k kernels (warp rounds for k <= 64, bitonic sort above)
+    against a stable numpy sort: descending value, equal values by smaller
+    index; rows with many exact ties and with negative values included."""
+    rng = np.random.default_rng(k)
+    z = rng.normal(0, 1, (6, 4096)).astype(np.float32)
+    z[1] = np.round(z[1] * 2) / 2 + np.float32(0.0)   # many exact ties (no negative zeros)
+    z[2] = -np.abs(z[2])                              # all negative
+    z[3] = 0.0                                        # all equal
+    z[4, ::7] = 5.0                                   # a tied top group
+    got = tg.probe_topk(torch.from_numpy(z).cuda(), k).cpu().numpy()
+    for r in range(z.shape[0]):
+        order = np.lexsort((np.arange(4096), -z[r].astype(np.float64)))
+        assert np.array_equal(got[r], order[:k]), (k, r)
+
+
 def test_save_load_round_trip(tmp_path):
     params = _params(9)
     tg.proposer_set(params)
