@@ -237,6 +237,25 @@ tsallis_status tsallis_segment(tsallis_ctx* ctx, const int16_t* d_vol, int64_t n
                                const tsallis_params* p, uint8_t* d_mask, int32_t* d_t, float* d_phi,
                                int32_t* d_status, cudaStream_t stream);
 
+/*
+ * tsallis_segment from and to HOST memory: h_vol (int16 [nz][ny][nx]) is
+ * read and h_mask (uint8, same shape), h_t, h_phi, h_status (as for
+ * tsallis_segment) are written by the call's copies. In the per-slice 1-D
+ * form the volume is pipelined in chunks of about 2^24 voxels (whole slices)
+ * through two device buffers on internal streams, so that copying chunk i+1
+ * in, segmenting chunk i and copying the mask of chunk i-1 out overlap; the
+ * other forms copy the volume in, segment it and copy the results out. The
+ * context owns the device buffers (grown on demand). Asynchronous: the work
+ * is ordered after what `stream` already holds and `stream` waits for all of
+ * it, so the host buffers may be read after synchronising `stream`. The copies
+ * overlap only when the host buffers are page-locked (cudaHostAlloc or
+ * cudaHostRegister); pageable memory works, more slowly. Errors as for
+ * tsallis_segment (no alignment rule for the host buffers).
+ */
+tsallis_status tsallis_segment_host(tsallis_ctx* ctx, const int16_t* h_vol, int64_t nx, int64_t ny, int64_t nz,
+                                    const tsallis_params* p, uint8_t* h_mask, int32_t* h_t, float* h_phi,
+                                    int32_t* h_status, cudaStream_t stream);
+
 /* One volume of a batch: device pointers and its shape. */
 typedef struct {
     const int16_t* vol;

@@ -96,6 +96,7 @@ _SIGS = {
     "tsallis_search": ([_P, _P, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
     "tsallis_binarize": ([_P, _P, _I64, _I64, _I64, _P, ctypes.POINTER(Params), _P, _P], ctypes.c_int),
     "tsallis_segment": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
+    "tsallis_segment_host": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
     "tsallis_segment_batch": ([_P, ctypes.POINTER(Volume), ctypes.c_int32, ctypes.POINTER(Params), _P, _P, _P, _P],
                               ctypes.c_int),
     "tsallis_autotune_batch": ([_P, ctypes.POINTER(Volume), ctypes.c_int32, ctypes.POINTER(Params), _P, _P, _P, _P,
@@ -547,3 +548,34 @@ def probe_topk(z: torch.Tensor, k: int) -> torch.Tensor:
     _check("tsallis_probe_topk", lib().tsallis_probe_topk(context(z.device), z.data_ptr(), B, int(k), out.data_ptr(),
                                                           _stream(z)))
     return out
+
+
+def tsallis_segment_host(vol: torch.Tensor, p: Params | None = None, mask: torch.Tensor | None = None,
+                         t: torch.Tensor | None = None, phi: torch.Tensor | None = None,
+                         status: torch.Tensor | None = None, device=None, sync: bool = True):
+    """Steps 1-4 from and to host memory (CPU tensors; page-locked ones let
+    the copies overlap the kernels): (mask, t, phi, status) on the host.
+    With sync=False the call returns once the work is enqueued on the
+    device's current stream; the outputs are valid after synchronising it."""
+    p = p or tsallis_params()
+    if not isinstance(vol, torch.Tensor) or vol.is_cuda or vol.dtype != torch.int16 or not vol.is_contiguous():
+        raise TypeError("volume must be a contiguous int16 CPU tensor")
+    nz, ny, nx = (1,) + tuple(vol.shape) if vol.dim() == 2 else tuple(vol.shape)
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index)
+    nh = nz if p.mode == PER_SLICE else 1
+    pin = vol.is_pinned()
+    if mask is None:
+        mask = torch.empty(vol.shape, dtype=torch.uint8, pin_memory=pin)
+    if t is None:
+        t = torch.empty((nh, 2) if p.two_d else (nh,), dtype=torch.int32, pin_memory=pin)
+    if phi is None:
+        phi = torch.empty(nh, dtype=torch.float32, pin_memory=pin)
+    if status is None:
+        status = torch.empty(nh, dtype=torch.int32, pin_memory=pin)
+    stream = torch.cuda.current_stream(dev)
+    _check("tsallis_segment_host", lib().tsallis_segment_host(
+        context(dev), vol.data_ptr(), nx, ny, nz, ctypes.byref(p), mask.data_ptr(), t.data_ptr(), phi.data_ptr(),
+        status.data_ptr(), stream.cuda_stream))
+    if sync:
+        stream.synchronize()
+    return mask, t, phi, status

@@ -88,6 +88,13 @@ struct tsallis_ctx {
     void* pred_buf = nullptr;
     int pred_cap = 0;
     unsigned* check = nullptr;    // checked build: first failing index check (checked.cuh)
+    // host-buffer entry point: device chunk buffers and outputs, internal
+    // streams (copy in, compute, copy out) and the events that order them
+    void* hp_buf = nullptr;
+    size_t hp_bytes = 0;
+    cudaStream_t hp_stream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t hp_ev[8] = {};
+    bool hp_ready = false;
 };
 
 namespace {
@@ -659,6 +666,11 @@ void tsallis_destroy(tsallis_ctx* c) {
         if (c->prop_x) cudaFree(c->prop_x);
         if (c->pred_buf) cudaFree(c->pred_buf);
         if (c->check) cudaFree(c->check);
+        if (c->hp_buf) cudaFree(c->hp_buf);
+        if (c->hp_ready) {
+            for (cudaStream_t& h : c->hp_stream) cudaStreamDestroy(h);
+            for (cudaEvent_t& e : c->hp_ev) cudaEventDestroy(e);
+        }
     }
     delete c;
 }
@@ -1504,4 +1516,110 @@ tsallis_status tsallis_probe_topk(tsallis_ctx* c, const float* d_logits, int32_t
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
     return cuda_status(mlp_topk(d_logits, B, k, d_out, stream));
+}
+
+// ------------------------------------------------------------ host buffers
+
+namespace {
+constexpr long long kHostChunkVox = 1ll << 24;   // voxels per pipelined chunk (32 MB of int16)
+
+tsallis_status ensure_host_pipeline(tsallis_ctx* c, size_t bytes) {
+    if (!c->hp_ready) {
+        for (cudaStream_t& h : c->hp_stream)
+            if (cudaStreamCreateWithFlags(&h, cudaStreamNonBlocking) != cudaSuccess) return TSALLIS_ERR_CUDA;
+        for (cudaEvent_t& e : c->hp_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return TSALLIS_ERR_CUDA;
+        c->hp_ready = true;
+    }
+    if (c->hp_buf && c->hp_bytes >= bytes) return TSALLIS_OK;
+    if (c->hp_buf) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
+        cudaFree(c->hp_buf);
+        c->hp_buf = nullptr;
+        c->hp_bytes = 0;
+    }
+    if (cudaMalloc(&c->hp_buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return TSALLIS_ERR_OOM;
+    }
+    c->hp_bytes = bytes;
+    return TSALLIS_OK;
+}
+}  // namespace
+
+tsallis_status tsallis_segment_host(tsallis_ctx* c, const int16_t* h_vol, int64_t nx, int64_t ny, int64_t nz,
+                                    const tsallis_params* p, uint8_t* h_mask, int32_t* h_t, float* h_phi,
+                                    int32_t* h_status, cudaStream_t stream) {
+    TSL_TRACE();
+    tsallis_status st = check_params(p);
+    if (st != TSALLIS_OK) return st;
+    if ((st = check_shape(nx, ny, nz)) != TSALLIS_OK) return st;
+    if (nz == 0) return TSALLIS_OK;
+    if (!c || !h_vol || !h_mask || !h_t || !h_phi || !h_status) return TSALLIS_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok()) return TSALLIS_ERR_CUDA;
+    const long long slice = nx * ny;
+    const long long nh = p->mode == TSALLIS_PER_SLICE ? nz : 1;
+    const long long tper = p->two_d ? 2 : 1;
+    // independent slices are pipelined in chunks; anything else is one chunk
+    const bool chunked = p->mode == TSALLIS_PER_SLICE && !p->two_d && p->topk == 0;
+    long long S = nz;
+    if (chunked) {
+        S = kHostChunkVox / slice;
+        if (S < 1) S = 1;
+        if (S > nz) S = nz;
+    }
+    const long long nchunks = (nz + S - 1) / S;
+    const int nbuf = nchunks > 1 ? 2 : 1;
+    const size_t in_b = align256((size_t)(S * slice) * sizeof(int16_t)), mask_b = align256((size_t)(S * slice));
+    const size_t out_b = align256((size_t)(nh * tper) * sizeof(int32_t)) + 2 * align256((size_t)nh * 4);
+    if ((st = ensure_host_pipeline(c, nbuf * (in_b + mask_b) + out_b)) != TSALLIS_OK) return st;
+    unsigned char* base = static_cast<unsigned char*>(c->hp_buf);
+    int16_t* din[2] = {reinterpret_cast<int16_t*>(base), reinterpret_cast<int16_t*>(base + in_b)};
+    uint8_t* dmask[2] = {base + nbuf * in_b, base + nbuf * in_b + mask_b};
+    unsigned char* ob = base + nbuf * (in_b + mask_b);
+    int32_t* dt = reinterpret_cast<int32_t*>(ob);
+    float* dphi = reinterpret_cast<float*>(ob + align256((size_t)(nh * tper) * sizeof(int32_t)));
+    int32_t* dst = reinterpret_cast<int32_t*>(ob + align256((size_t)(nh * tper) * sizeof(int32_t)) +
+                                              align256((size_t)nh * 4));
+    cudaStream_t s_in = c->hp_stream[0], s_comp = c->hp_stream[1], s_out = c->hp_stream[2];
+    cudaEvent_t ev_start = c->hp_ev[0], ev_done = c->hp_ev[1];
+    cudaEvent_t* ev_in = &c->hp_ev[2];     // [2]
+    cudaEvent_t* ev_comp = &c->hp_ev[4];   // [2]
+    cudaEvent_t* ev_out = &c->hp_ev[6];    // [2]
+    auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    // the internal streams start after the caller's earlier work
+    if (!ok(cudaEventRecord(ev_start, stream)) || !ok(cudaStreamWaitEvent(s_in, ev_start, 0)) ||
+        !ok(cudaStreamWaitEvent(s_comp, ev_start, 0)) || !ok(cudaStreamWaitEvent(s_out, ev_start, 0)))
+        return TSALLIS_ERR_CUDA;
+    for (long long i = 0; i < nchunks; ++i) {
+        const int b = (int)(i & 1);
+        const long long z0 = i * S, Si = nz - z0 < S ? nz - z0 : S;
+        const size_t nv = (size_t)(Si * slice);
+        // copy in (after the chunk two back has been segmented out of this buffer)
+        if (i >= 2 && !ok(cudaStreamWaitEvent(s_in, ev_comp[b], 0))) return TSALLIS_ERR_CUDA;
+        if (!ok(cudaMemcpyAsync(din[b], h_vol + z0 * slice, nv * sizeof(int16_t), cudaMemcpyHostToDevice, s_in)) ||
+            !ok(cudaEventRecord(ev_in[b], s_in)))
+            return TSALLIS_ERR_CUDA;
+        // segment (after its input arrived and the mask buffer was copied out)
+        if (!ok(cudaStreamWaitEvent(s_comp, ev_in[b], 0))) return TSALLIS_ERR_CUDA;
+        if (i >= 2 && !ok(cudaStreamWaitEvent(s_comp, ev_out[b], 0))) return TSALLIS_ERR_CUDA;
+        const long long h0 = chunked ? z0 : 0;
+        if ((st = tsallis_segment(c, din[b], nx, ny, Si, p, dmask[b], dt + h0 * tper, dphi + h0, dst + h0, s_comp)) !=
+            TSALLIS_OK)
+            return st;
+        if (!ok(cudaEventRecord(ev_comp[b], s_comp))) return TSALLIS_ERR_CUDA;
+        // copy the mask out
+        if (!ok(cudaStreamWaitEvent(s_out, ev_comp[b], 0)) ||
+            !ok(cudaMemcpyAsync(h_mask + z0 * slice, dmask[b], nv, cudaMemcpyDeviceToHost, s_out)) ||
+            !ok(cudaEventRecord(ev_out[b], s_out)))
+            return TSALLIS_ERR_CUDA;
+    }
+    // thresholds, values and statuses; then the caller's stream waits for it all
+    if (!ok(cudaMemcpyAsync(h_t, dt, (size_t)(nh * tper) * sizeof(int32_t), cudaMemcpyDeviceToHost, s_out)) ||
+        !ok(cudaMemcpyAsync(h_phi, dphi, (size_t)nh * sizeof(float), cudaMemcpyDeviceToHost, s_out)) ||
+        !ok(cudaMemcpyAsync(h_status, dst, (size_t)nh * sizeof(int32_t), cudaMemcpyDeviceToHost, s_out)) ||
+        !ok(cudaEventRecord(ev_done, s_out)) || !ok(cudaStreamWaitEvent(stream, ev_done, 0)))
+        return TSALLIS_ERR_CUDA;
+    return TSALLIS_OK;
 }

@@ -316,3 +316,34 @@ def test_double_float_pow_and_log2_accuracy():
             assert rel.max() < 1e-12, (N, q, rel.max(), hs[np.argmax(rel)])
         wl = np.log2(hs.astype(np.float64))
         assert np.max(np.abs(lg - wl) / np.maximum(wl, 1.0)) < 1e-13
+
+
+# ------------------------------------------------------------ host buffers
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_segment_host_full_size_equals_device(pinned):
+    """The 512x512x400 chest volume through the host-buffer entry point (7
+    pipelined chunks of 64 slices): masks, thresholds, values and statuses
+    equal the device path's."""
+    v = phantom.generate_cuda(phantom.chest_volume(2012106842, 512, 512, 400))
+    p = tg.tsallis_params(q=0.8, mode="slice")
+    m0, t0, phi0, st0 = tg.tsallis_segment(v, p)
+    hv = v.cpu()
+    if pinned:
+        hv = hv.pin_memory()
+    m, t, phi, st = tg.tsallis_segment_host(hv, p)
+    assert torch.equal(m, m0.cpu()) and torch.equal(t, t0.cpu())
+    assert torch.equal(phi, phi0.cpu()) and torch.equal(st, st0.cpu())
+
+
+@pytest.mark.parametrize("shape,mode,two_d", [((3, 37, 53), "slice", False), ((2, 300, 301), "volume", False),
+                                              ((70, 512, 520), "slice", False), ((4, 64, 64), "slice", True),
+                                              ((5, 48, 40), "volume", True)])
+def test_segment_host_shapes_and_forms(shape, mode, two_d):
+    rng = np.random.default_rng(sum(shape))
+    hv = torch.from_numpy(rng.integers(-1500, 3200, shape).astype(np.int16))
+    p = tg.tsallis_params(q=0.8, mode=mode, two_d=two_d)
+    m0, t0, phi0, st0 = tg.tsallis_segment(hv.cuda(), p)
+    m, t, phi, st = tg.tsallis_segment_host(hv, p)
+    assert torch.equal(m, m0.cpu()) and torch.equal(t, t0.cpu())
+    assert torch.equal(phi, phi0.cpu()) and torch.equal(st, st0.cpu())
