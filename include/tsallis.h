@@ -23,8 +23,10 @@
  *   - Volumes are int16 Hounsfield values laid out [nz][ny][nx], x fastest,
  *     contiguous. Masks are uint8 [nz][ny][nx] holding 0 or 1.
  *   - Volume and mask base pointers must be 16-byte aligned (any cudaMalloc
- *     result is); otherwise TSALLIS_ERR_ALIGNMENT is returned. Any nx, ny, nz
- *     is accepted; ragged tails are handled inside the kernels.
+ *     result is) unless an entry point states its own rule
+ *     (tsallis_preprocess, tsallis_segment_host); otherwise
+ *     TSALLIS_ERR_ALIGNMENT is returned. Any nx, ny, nz is accepted; ragged
+ *     tails are handled inside the kernels.
  *   - Argument, size and alignment errors are returned synchronously, before
  *     anything is enqueued. Data-dependent outcomes (no valid threshold, a
  *     device wait that ran out) are written per histogram to d_status and are
@@ -59,7 +61,9 @@ typedef enum {
 #define TSALLIS_STATUS_WINDOW_HIT 0x400    /* window search: the maximiser was among the
                                             proposed candidates */
 #define TSALLIS_STATUS_FALLBACK_SHIFT 16   /* window search: bits 16..23 hold how many
-                                              64-level blocks were searched exhaustively */
+                                              64-level blocks (1-D) or 4x4-pair cells (2-D,
+                                              saturating at 255) beyond the proposals were
+                                              searched exhaustively */
 #define TSALLIS_STATUS_FIRST_PASS_EXACT 0x200  /* the mask written in the histogram pass with a
                                                   predicted threshold was already exact, so the
                                                   group was not read a second time */
@@ -113,8 +117,9 @@ typedef struct {
     int32_t shift;    /* 2-D only: grey level = b >> shift, giving L2 = nbins >> shift
                          levels (2..256); default 4 */
     int32_t topk;     /* 0: exhaustive search (default); 1..256: window search of the
-                         proposer's topk candidates, certified by per-block bounds
-                         (needs a proposer, see tsallis_proposer_set; 1-D, nbins 4096) */
+                         proposer's topk candidates, certified by per-block bounds;
+                         1-D: nbins 4096 and proposer slot 0; 2-D: 256 grey levels and
+                         slot 1 (see tsallis_proposer_set and tsallis_proposer_select) */
     uint32_t flags;   /* TSALLIS_FLAG_* */
 } tsallis_params;
 
@@ -228,7 +233,8 @@ tsallis_status tsallis_binarize(tsallis_ctx* ctx, const int16_t* d_vol, int64_t 
 /*
  * Steps 1-4 fused in one persistent kernel (1-D form): per-slice histograms
  * are built, searched by the last tile to arrive, and the slice is binarised
- * while it is still in L2.
+ * by the same launch (its second read can hit L2 when it comes soon enough
+ * after the first; on large volumes most of it comes from memory).
  *   d_mask out [nz][ny][nx]; d_t, d_phi, d_status out [nh] as in
  *   tsallis_search (nh = nz per slice, 1 whole volume).
  * The 2-D form is dispatched to its own kernels by the same call.
