@@ -126,3 +126,32 @@ def test_preprocess_histograms_count_every_voxel():
     assert o.dtype == np.int16 and o.min() >= 0 and o.max() <= 255
     _, hv = oracle.preprocess(v, r=2, per_slice=False)
     assert np.array_equal(hv[0], h.sum(axis=0))
+
+
+def _divider(D):
+    """The level map's division by 2D as the kernel does it: a 32-bit
+    multiply-high and a shift, m = floor(2^(32+s) / d) + 1 with
+    s = max(ceil(log2 d) - 2, 0), d = 2D."""
+    d = 2 * D
+    l = int(np.ceil(np.log2(d))) if d > 1 else 0
+    while (1 << l) < d:
+        l += 1
+    s = max(l - 2, 0)
+    return ((1 << (32 + s)) // d) + 1, s
+
+
+def test_level_map_divider_is_exact_for_every_range():
+    """For range widths D = hu_max - hu_min from 1 to 65535 (a sample plus
+    both ends and every power of two), the multiplier fits 32 bits and
+    umulhi(n, m) >> s equals n // (2D) for every n = 2 c 255 + D the map
+    forms (c = 0..D): the division the pre-processing kernel avoids."""
+    rng = np.random.default_rng(11)
+    Ds = sorted(set([1, 2, 3, 4500, 4096, 65535] + [1 << k for k in range(16)] + [(1 << k) + 1 for k in range(16)] +
+                    list(rng.integers(1, 65536, 120))))
+    for D in Ds:
+        m, s = _divider(int(D))
+        assert m < (1 << 32), D
+        c = np.arange(D + 1, dtype=np.uint64)
+        n = np.uint64(2 * 255) * c + np.uint64(D)
+        got = ((n * np.uint64(m)) >> np.uint64(32)) >> np.uint64(s)
+        assert np.array_equal(got, n // np.uint64(2 * D)), D
