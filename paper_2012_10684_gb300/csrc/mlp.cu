@@ -224,7 +224,8 @@ __device__ __forceinline__ void warp_topk_rounds(unsigned long long (&key)[kPer]
     }
 }
 __global__ void __launch_bounds__(512) k_topk_small(const float* __restrict__ z, int k, int32_t* __restrict__ out) {
-    __shared__ unsigned long long cand[16][kTopkSmallMax];
+    __shared__ unsigned long long cand[16 * kTopkSmallMax];   // warp w's k keys at [w * k, w * k + k)
+    __shared__ unsigned long long fin[kTopkSmallMax];
     const int row = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float* zr = z + (long long)row * kMlpOut;
     unsigned long long key[8];
@@ -233,19 +234,37 @@ __global__ void __launch_bounds__(512) k_topk_small(const float* __restrict__ z,
         const int i = warp * 256 + j * 32 + lane;
         key[j] = topk_key(zr[i], i);
     }
-    warp_topk_rounds<8>(key, k, cand[warp]);
+    warp_topk_rounds<8>(key, k, cand + warp * k);
     __syncthreads();
     if (warp != 0) return;
-    // warp 0: lane l holds candidates l, l + 32, ... of the 16 k (at most 32 per lane)
-    unsigned long long key2[32];
+    // warp 0 merges the 16 k candidates in shared memory: lane l owns
+    // candidates l, l + 32, ... and caches the largest it still holds; each
+    // round takes the warp's maximum, and only the lane that held it (keys
+    // are distinct) clears that candidate and looks for its next largest
+    const int nc = 16 * k;
+    auto rescan = [&](int& bi) {
+        unsigned long long b = 0ull;
+        bi = -1;
+        for (int c = lane; c < nc; c += 32)
+            if (cand[c] > b) { b = cand[c]; bi = c; }
+        return b;
+    };
+    int bi;
+    unsigned long long mine = rescan(bi);
+    for (int r = 0; r < k; ++r) {
+        unsigned long long best = mine;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int c = j * 32 + lane;
-        key2[j] = c < 16 * k ? cand[c / k][c % k] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+            best = other > best ? other : best;
+        }
+        if (lane == 0) fin[r] = best;
+        if (mine == best && mine != 0ull) {
+            cand[bi] = 0ull;
+            mine = rescan(bi);
+        }
+        __syncwarp();
     }
-    __shared__ unsigned long long fin[kTopkSmallMax];
-    warp_topk_rounds<32>(key2, k, fin);
-    __syncwarp();
     for (int r = lane; r < k; r += 32)
         out[(long long)row * k + r] = (int32_t)(0xffffffffu - (unsigned)(fin[r] & 0xffffffffu));
 }
