@@ -79,8 +79,14 @@ typedef enum {
 } tsallis_polarity;
 
 /* Debug flags (tests only). */
-#define TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL 0x1u /* the first histogram tile never reports
-                                                arrival, so waits on its histogram run out */
+#define TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL 0x1u /* tile and cluster kernels: the first histogram
+                                                tile never reports arrival, so waits on its
+                                                histogram run out and its group reports
+                                                TSALLIS_ERR_TIMEOUT; predicted first-pass kernel:
+                                                one block never arrives at the grid barrier
+                                                after the streaming phase, the barrier's wait
+                                                runs out and every slice of the call reports
+                                                TSALLIS_ERR_TIMEOUT */
 /* tsallis_segment_batch, whole-volume mode: binarise in the histogram pass
  * with a threshold predicted from the histogram of the middle sixteenth of
  * each volume's slices, by the proposer (PREDICT_PROPOSER; needs one, see
@@ -154,7 +160,7 @@ tsallis_status tsallis_set_launch_shape(tsallis_ctx* ctx, int32_t tile_vox, int3
 
 /*
  * Kernel used by tsallis_segment for per-slice 1-D work (the paper has one
- * GPU design; these are two GB300 designs of the same steps, with equal
+ * GPU design; these are GB300 designs of the same steps, with equal
  * results):
  *   TSALLIS_SLICE_KERNEL_AUTO (default): the persistent tile kernel;
  *   TSALLIS_SLICE_KERNEL_TILES: the persistent tile kernel;
@@ -162,14 +168,31 @@ tsallis_status tsallis_set_launch_shape(tsallis_ctx* ctx, int32_t tile_vox, int3
  *     (slices of at most 262144 voxels whose voxel count is a multiple of
  *     8), else the tile kernel. Returns TSALLIS_ERR_UNIMPLEMENTED if the
  *     device cannot run 8-CTA clusters.
- * The cluster kernel holds each slice in the shared memory of an 8-CTA
- * thread-block cluster between its histogram and its binarisation, so the
- * volume is read from memory once; it is slower than the tile kernel
+ *   TSALLIS_SLICE_KERNEL_PREDICT: the predicted first-pass kernel where it
+ *     applies (slices whose voxel count is a multiple of 8 and at most
+ *     2^24; topk = 0), else the tile kernel.
+ * The predicted first-pass kernel reads every voxel once in the usual case:
+ * a predicted threshold t^ per slice (the exhaustive search, in FP32, of
+ * the histogram of every 16th row of the slice; see tsallis_set_prediction)
+ * lets the histogram pass also write the mask (Algorithm 1 at t^) and list
+ * the voxels whose level lies within the prediction window of t^; after the
+ * slice's exact search gives t, the listed voxels whose side changes are
+ * rewritten. A slice is read a second time only when t lies outside the
+ * window, the subsample has fewer than two non-empty levels, or a warp's
+ * list overflows (a warp keeps up to max(256, 1/16 of the voxels it counts)
+ * entries; a grid barrier that runs out of time makes every slice of the
+ * call report TSALLIS_ERR_TIMEOUT instead). Slices whose mask needed
+ * no second read carry TSALLIS_STATUS_FIRST_PASS_EXACT. The tile kernel
+ * reads each slice twice, the second time mostly from L2 when it comes soon
+ * enough. The cluster kernel holds each slice in the shared memory of an
+ * 8-CTA thread-block cluster between its histogram and its binarisation,
+ * so the volume is read from memory once; it is slower than the others
  * (each cluster waits for its slice's search before taking the next).
  */
 #define TSALLIS_SLICE_KERNEL_AUTO 0
 #define TSALLIS_SLICE_KERNEL_TILES 1
 #define TSALLIS_SLICE_KERNEL_CLUSTER 2
+#define TSALLIS_SLICE_KERNEL_PREDICT 3
 tsallis_status tsallis_set_slice_kernel(tsallis_ctx* ctx, int32_t kind);
 
 /*
@@ -187,6 +210,16 @@ tsallis_status tsallis_set_slice_kernel(tsallis_ctx* ctx, int32_t kind);
  * either way; only the memory traffic differs.
  */
 tsallis_status tsallis_set_speculation(tsallis_ctx* ctx, int32_t on);
+
+/*
+ * Settings of the predicted first-pass kernel (TSALLIS_SLICE_KERNEL_PREDICT):
+ * the prediction histograms every row_stride-th row of a slice (1..4096,
+ * default 16; a slice of fewer rows uses its middle row), and the voxels the
+ * first pass lists are those whose level lies in (t^ - window, t^ + window]
+ * (1..127, default 8). Both only trade memory traffic against work; results
+ * are the same for every setting. TSALLIS_ERR_INVALID_ARG outside the ranges.
+ */
+tsallis_status tsallis_set_prediction(tsallis_ctx* ctx, int32_t row_stride, int32_t window);
 
 /*
  * Step 1: histogram (section I "Thresholding", Fig. 2; 2-D: section II-C,

@@ -35,6 +35,15 @@ tsallis_status tsallis_probe_topk(tsallis_ctx* ctx, const float* d_logits, int32
                                   cudaStream_t stream);
 
 /*
+ * Predicted first-pass kernel: with on = 1 its prediction phase publishes no
+ * prediction, so nothing is binarised in the first pass and every slice is
+ * binarised after its search; results must be unchanged (statuses then lack
+ * TSALLIS_STATUS_FIRST_PASS_EXACT). on = 0 restores normal operation.
+ * TSALLIS_ERR_INVALID_ARG for a null context or another value of on.
+ */
+tsallis_status tsallis_test_withhold_predictions(tsallis_ctx* ctx, int32_t on);
+
+/*
  * Checked build only (the library compiled with -DTSALLIS_CHECKED): the
  * kernels test the indices they compute against the extents of the buffers
  * they address, skip an access that fails and record the first failing
@@ -43,7 +52,8 @@ tsallis_status tsallis_probe_topk(tsallis_ctx* ctx, const float* d_logits, int32
  * returns TSALLIS_ERR_UNIMPLEMENTED. Site numbers: 101-103 the tile kernel
  * (group, tile, binarise queue), 201-206 pre-processing (staged word, voxel
  * read, disk window, intermediate word, output voxel, histogram level),
- * 301-303 the 2-D search (table entries, candidate cell, brute-force row).
+ * 301-303 the 2-D search (table entries, candidate cell, brute-force row),
+ * 401-402 the predicted first-pass kernel (job slice, rewritten position).
  */
 tsallis_status tsallis_check_status(tsallis_ctx* ctx, uint32_t* site);
 

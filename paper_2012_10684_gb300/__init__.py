@@ -43,7 +43,7 @@ TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL = 0x1
 TSALLIS_FLAG_PREDICT_PROPOSER = 0x2
 TSALLIS_FLAG_PREDICT_SUBSAMPLE = 0x4
 TSALLIS_FLAG_BRUTE_FORCE_2D = 0x8
-SLICE_KERNELS = {"auto": 0, "tiles": 1, "cluster": 2}
+SLICE_KERNELS = {"auto": 0, "tiles": 1, "cluster": 2, "predict": 3}
 
 PER_SLICE, WHOLE_VOLUME = 0, 1
 MASK_LOW, MASK_HIGH = 0, 1
@@ -92,6 +92,8 @@ _SIGS = {
     "tsallis_set_launch_shape": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "tsallis_set_slice_kernel": ([_P, ctypes.c_int32], ctypes.c_int),
     "tsallis_set_speculation": ([_P, ctypes.c_int32], ctypes.c_int),
+    "tsallis_set_prediction": ([_P, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "tsallis_test_withhold_predictions": ([_P, ctypes.c_int32], ctypes.c_int),
     "tsallis_histogram": ([_P, _P, _I64, _I64, _I64, ctypes.POINTER(Params), _P, _P], ctypes.c_int),
     "tsallis_search": ([_P, _P, _I64, ctypes.POINTER(Params), _P, _P, _P, _P, _P], ctypes.c_int),
     "tsallis_binarize": ([_P, _P, _I64, _I64, _I64, _P, ctypes.POINTER(Params), _P, _P], ctypes.c_int),
@@ -184,8 +186,8 @@ def set_launch_shape(tile_vox: int = 65536, blocks_per_sm: int = 0, device=None)
 
 
 def set_slice_kernel(kind: str = "auto", device=None) -> None:
-    """Kernel for per-slice 1-D segmentation: "auto", "tiles" or "cluster"
-    (see tsallis_set_slice_kernel)."""
+    """Kernel for per-slice 1-D segmentation: "auto", "tiles", "cluster" or
+    "predict" (see tsallis_set_slice_kernel)."""
     _check("tsallis_set_slice_kernel", lib().tsallis_set_slice_kernel(context(device), SLICE_KERNELS[kind]))
 
 
@@ -193,6 +195,19 @@ def set_speculation(on: bool = False, device=None) -> None:
     """First-pass binarisation with a predicted threshold in the tile kernel
     (see tsallis_set_speculation)."""
     _check("tsallis_set_speculation", lib().tsallis_set_speculation(context(device), 1 if on else 0))
+
+
+def set_prediction(row_stride: int = 8, window: int = 8, device=None) -> None:
+    """Prediction row stride and list window of the predicted first-pass
+    kernel (see tsallis_set_prediction)."""
+    _check("tsallis_set_prediction", lib().tsallis_set_prediction(context(device), int(row_stride), int(window)))
+
+
+def withhold_predictions(on: bool, device=None) -> None:
+    """Test hook: the predicted first-pass kernel publishes no predictions
+    (see tsallis_test_withhold_predictions)."""
+    _check("tsallis_test_withhold_predictions",
+           lib().tsallis_test_withhold_predictions(context(device), 1 if on else 0))
 
 
 def tsallis_probe_dfmath(h: torch.Tensor, N: int, q: float):

@@ -68,6 +68,15 @@ struct tsallis_ctx {
     int slice_kernel = TSALLIS_SLICE_KERNEL_AUTO;
     int speculate = 0;            // tile kernel: binarise in the first pass with a predicted threshold
     int cluster_max = 0;
+    // per-slice kernel that reads each voxel once: prediction settings, its
+    // resident blocks per SM, a test switch, and its arrays (spec_layout)
+    int spec_stride = 16;
+    int spec_win = 8;
+    int spec_blocks_per_sm = 0;
+    unsigned spec_test_flags = 0;
+    void* spec_buf = nullptr;       // predicted thresholds, flags, queue, tile counts, lists
+    size_t spec_bytes = 0;
+    long long spec_nz = 0, spec_ntot = 0, spec_nl = 0, spec_nexc = 0;   // the layout it holds
     // term table of the per-slice search (built for one slice size and q)
     float2* ptab = nullptr;
     long long ptab_cap = 0;     // entries allocated
@@ -542,6 +551,131 @@ bool use_slice_cluster(const tsallis_ctx* c, const tsallis_params* p, long long 
            slice <= (long long)kClusterCtas * kClusterPartVox;
 }
 
+// The predicted first-pass kernel (when selected) takes per-slice 1-D work
+// whose slices are whole 16-byte words of at most kSpecMaxSlice voxels.
+bool use_slice_spec(const tsallis_ctx* c, const tsallis_params* p, long long slice, long long nz) {
+    if (c->slice_kernel != TSALLIS_SLICE_KERNEL_PREDICT) return false;
+    return p->mode == TSALLIS_PER_SLICE && !p->two_d && p->topk == 0 && slice % 8 == 0 &&
+           slice <= kSpecMaxSlice && nz <= (1 << 19);   // queue entries hold the slice in 20 bits
+}
+
+// Arrays of the predicted first-pass kernel in one buffer (grown, never
+// shrunk; zeroed when allocated): predicted thresholds [nz] (u64), slice
+// flags [nz], second-pass queue [nz * npiece], list starts and lengths
+// [grid * nseg * 16] each, lists [grid * 16 * wcap]. The kernel leaves the
+// thresholds and flags zeroed; the others are written before they are read.
+struct SpecView {
+    unsigned long long* pred;
+    int* sflag;
+    unsigned* rbq;
+    int* toff;
+    int* tcnt;
+    unsigned* exc;
+};
+inline size_t spec_layout(long long nz, long long nq, long long nl, long long nexc, SpecView* v, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) & ~size_t(255);
+        return o;
+    };
+    const size_t o_pred = take((size_t)nz * 8), o_flag = take((size_t)nz * 4), o_rbq = take((size_t)nq * 4),
+                 o_toff = take((size_t)nl * 4), o_tcnt = take((size_t)nl * 4), o_exc = take((size_t)nexc * 4);
+    if (v) {
+        v->pred = reinterpret_cast<unsigned long long*>(base + o_pred);
+        v->sflag = reinterpret_cast<int*>(base + o_flag);
+        v->rbq = reinterpret_cast<unsigned*>(base + o_rbq);
+        v->toff = reinterpret_cast<int*>(base + o_toff);
+        v->tcnt = reinterpret_cast<int*>(base + o_tcnt);
+        v->exc = reinterpret_cast<unsigned*>(base + o_exc);
+    }
+    return off;
+}
+
+// A buffer is reused only for the same layout; a new layout gets a new
+// zeroed buffer.
+tsallis_status ensure_spec(tsallis_ctx* c, long long nz, long long nq, long long nl, long long nexc, SpecView* v) {
+    const size_t bytes = spec_layout(nz, nq, nl, nexc, nullptr, nullptr);
+    const bool same = c->spec_buf && c->spec_nz == nz && c->spec_ntot == nq && c->spec_nl == nl && c->spec_nexc == nexc;
+    if (!same) {
+        if (c->spec_buf) {
+            if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
+            cudaFree(c->spec_buf);
+            c->spec_buf = nullptr;
+            c->spec_bytes = 0;
+        }
+        if (cudaMalloc(&c->spec_buf, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return TSALLIS_ERR_OOM;
+        }
+        if (cudaMemset(c->spec_buf, 0, bytes) != cudaSuccess) return TSALLIS_ERR_CUDA;
+        c->spec_bytes = bytes;
+        c->spec_nz = nz;
+        c->spec_ntot = nq;
+        c->spec_nl = nl;
+        c->spec_nexc = nexc;
+    }
+    spec_layout(nz, nq, nl, nexc, v, static_cast<char*>(c->spec_buf));
+    return TSALLIS_OK;
+}
+
+tsallis_status segment_spec(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                            const tsallis_params* p, uint8_t* d_mask, int32_t* d_t, float* d_phi, int32_t* d_status,
+                            cudaStream_t stream) {
+    const long long S = nx * ny, V = S * nz;
+    const long long G = (long long)c->sm_count * c->spec_blocks_per_sm;
+    // the largest range of a block, the slices it can meet, the lists a warp keeps
+    const long long rmax = ((V / G + 7) / 8) * 8 + 8;
+    const long long nseg = (rmax + S - 1) / S + 1;
+    const long long wcap = rmax / kSpecWarps / 16 > kSpecWarpList ? rmax / kSpecWarps / 16 : kSpecWarpList;
+    const int piece = 65536;
+    const long long npiece = (S + piece - 1) / piece;
+    if (npiece >= 4096) return TSALLIS_ERR_INVALID_ARG;
+    tsallis_status st;
+    if ((st = ensure_scratch(c, nz, 0)) != TSALLIS_OK) return st;
+    SpecView sv;
+    if ((st = ensure_spec(c, nz, nz * npiece, G * nseg * kSpecWarps, G * kSpecWarps * wcap, &sv)) != TSALLIS_OK)
+        return st;
+    SpecArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.vol = d_vol;
+    a.mask = d_mask;
+    a.slice_vox = S;
+    a.nvox = V;
+    a.nx = (int)nx;
+    a.ny = (int)ny;
+    a.nz = (int)nz;
+    a.nseg = (int)nseg;
+    a.wcap = (int)wcap;
+    a.piece_vox = piece;
+    a.npiece = (int)npiece;
+    a.sub_stride = c->spec_stride;
+    a.win = c->spec_win;
+    a.lo = p->lo;
+    a.L = p->nbins;
+    a.q = p->q;
+    a.polarity = p->polarity;
+    a.flags = (p->flags & TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL) | c->spec_test_flags;
+    a.timeout_ns = c->timeout_ns;
+    ScratchView v = view(c);
+    a.hdr = v.hdr;
+    a.ghist = v.ghist;
+    a.pred = sv.pred;
+    a.sflag = sv.sflag;
+    a.toff = sv.toff;
+    a.tcnt = sv.tcnt;
+    a.exc = sv.exc;
+    a.rbq = sv.rbq;
+    a.t_out = d_t;
+    a.phi_out = d_phi;
+    a.status = d_status;
+    a.df_tables = c->df_tables;
+    a.ptab = pow_table(c, S, p->q, stream);
+    a.ptab_n = S;
+    a.check = c->check;
+    return cuda_status(launch_slice_spec(a, (int)G, stream));
+}
+
 }  // namespace
 
 extern "C" {
@@ -609,6 +743,12 @@ tsallis_status tsallis_create(tsallis_ctx** out, int device) {
         cudaGetLastError();
         c->cluster_max = 0;   // the tile kernel serves every shape
     }
+    if (slice_spec_prepare() != cudaSuccess || slice_spec_occupancy(&c->spec_blocks_per_sm) != cudaSuccess ||
+        c->spec_blocks_per_sm < 1) {
+        cudaGetLastError();
+        delete c;
+        return TSALLIS_ERR_CUDA;
+    }
     if (preproc_prepare() != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -667,6 +807,7 @@ void tsallis_destroy(tsallis_ctx* c) {
         if (c->pred_buf) cudaFree(c->pred_buf);
         if (c->check) cudaFree(c->check);
         if (c->hp_buf) cudaFree(c->hp_buf);
+        if (c->spec_buf) cudaFree(c->spec_buf);
         if (c->hp_ready) {
             for (cudaStream_t& h : c->hp_stream) cudaStreamDestroy(h);
             for (cudaEvent_t& e : c->hp_ev) cudaEventDestroy(e);
@@ -692,7 +833,7 @@ tsallis_status tsallis_set_launch_shape(tsallis_ctx* c, int32_t tile_vox, int32_
 
 tsallis_status tsallis_set_slice_kernel(tsallis_ctx* c, int32_t kind) {
     if (!c || (kind != TSALLIS_SLICE_KERNEL_AUTO && kind != TSALLIS_SLICE_KERNEL_TILES &&
-               kind != TSALLIS_SLICE_KERNEL_CLUSTER))
+               kind != TSALLIS_SLICE_KERNEL_CLUSTER && kind != TSALLIS_SLICE_KERNEL_PREDICT))
         return TSALLIS_ERR_INVALID_ARG;
     if (kind == TSALLIS_SLICE_KERNEL_CLUSTER && c->cluster_max < 1) return TSALLIS_ERR_UNIMPLEMENTED;
     c->slice_kernel = kind;
@@ -702,6 +843,19 @@ tsallis_status tsallis_set_slice_kernel(tsallis_ctx* c, int32_t kind) {
 tsallis_status tsallis_set_speculation(tsallis_ctx* c, int32_t on) {
     if (!c || (on != 0 && on != 1)) return TSALLIS_ERR_INVALID_ARG;
     c->speculate = on;
+    return TSALLIS_OK;
+}
+
+tsallis_status tsallis_set_prediction(tsallis_ctx* c, int32_t row_stride, int32_t window) {
+    if (!c || row_stride < 1 || row_stride > 4096 || window < 1 || window > kSpecMaxWin) return TSALLIS_ERR_INVALID_ARG;
+    c->spec_stride = row_stride;
+    c->spec_win = window;
+    return TSALLIS_OK;
+}
+
+tsallis_status tsallis_test_withhold_predictions(tsallis_ctx* c, int32_t on) {
+    if (!c || (on != 0 && on != 1)) return TSALLIS_ERR_INVALID_ARG;
+    c->spec_test_flags = on ? kSpecDebugNoPrediction : 0u;
     return TSALLIS_OK;
 }
 
@@ -826,6 +980,8 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
         const tsallis_volume v{d_vol, d_mask, nx, ny, nz};
         return tsallis_segment_batch(c, &v, 1, p, d_t, d_phi, d_status, stream);
     }
+    if (use_slice_spec(c, p, slice, nz))
+        return segment_spec(c, d_vol, nx, ny, nz, p, d_mask, d_t, d_phi, d_status, stream);
     if (use_slice_cluster(c, p, slice)) {
         if ((st = ensure_scratch(c, 0, 0)) != TSALLIS_OK) return st;
         ClusterArgs a;

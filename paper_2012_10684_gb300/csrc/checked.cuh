@@ -35,6 +35,9 @@ enum CheckSite : unsigned {
     kSite2dTables = 301,      // 2-D search: table entries of a pair
     kSite2dCell = 302,        // 2-D window: candidate cell
     kSite2dBrute = 303,       // 2-D brute force: histogram row
+    kSiteSpecSlice = 401,     // predicted first pass: job's slice
+    kSiteSpecPatch = 402,     // predicted first pass: listed position rewritten
+    kSiteSpecQueue = 403,     // predicted first pass: second-pass queue position
 };
 
 }  // namespace tsl

@@ -21,13 +21,24 @@
 namespace tsl {
 
 // Tables, filled on the host in double precision and split into float
-// pairs. Stored in global memory (read with __ldg; indices diverge).
+// pairs. Stored in global memory; kernels copy them into shared memory
+// (df_stage) before use, since every power reads them at diverging indices
+// on its dependent path, where a global load costs a round trip to L2.
 struct DfTables {
     float4 lg[128];  // x: float(1 / c_j), c_j = 1 + (j + 0.5) / 128; y, z: -log2(x) as hi, lo
     float2 ex[65];   // 2^((j - 32) / 64) as hi, lo
     const float2* lt;   // log2(h) as hi, lo for 0 <= h <= lt_max (built on the device)
     int lt_max;
 };
+
+// Copies the tables (global memory) into dst (shared memory); threads
+// tid = 0 .. n-1 of the caller take part, and the caller synchronises them
+// before the copy is used. The big log2 table stays in global memory.
+__device__ __forceinline__ void df_stage(DfTables* dst, const DfTables* __restrict__ src, int tid, int n) {
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int i = tid; i < (int)(sizeof(DfTables) / sizeof(int)); i += n) d[i] = __ldg(s + i);
+}
 
 __device__ __forceinline__ F2 fast_two_sum(float a, float b) {
     float s = __fadd_rn(a, b);
@@ -83,7 +94,7 @@ static __device__ __noinline__ F2 df_log2_u32(unsigned h, const DfTables* __rest
     const float mh = hh.hi * sc, ml = hh.lo * sc;       // m = h / 2^e in [1, 2)
     int j = (int)((mh - 1.0f) * 128.0f);
     j = j > 127 ? 127 : j;
-    const float4 tj = __ldg(&T->lg[j]);
+    const float4 tj = T->lg[j];
     // r = m * inv_j - 1, |r| <= 2^-8
     F2 p = two_prod(mh, tj.x);
     F2 r = fast_two_sum(__fsub_rn(p.hi, 1.0f), __fmaf_rn(ml, tj.x, p.lo));
@@ -114,7 +125,7 @@ __device__ __forceinline__ F2 df_exp2(F2 y, const DfTables* __restrict__ T) {
     const float tail = xh * xh * xh * __fmaf_rn(xh, __fmaf_rn(xh, 8.33333376795e-3f, 4.16666679084e-2f),
                                                0.166666671634f);
     ex = df_add(ex, F2{tail, 0.f});
-    const float2 tj = __ldg(&T->ex[(int)jf + 32]);
+    const float2 tj = T->ex[(int)jf + 32];
     F2 r = df_mul(F2{tj.x, tj.y}, ex);
     const int ki = (int)k;
     return {ldexpf(r.hi, ki), ldexpf(r.lo, ki)};

@@ -22,7 +22,8 @@ struct ScratchHeader {
     int err;              // a device wait ran out or an arrival was skipped
     unsigned long long latest;   // (epoch + 1) << 32 | (t + 1): the threshold found
                                  // most recently in this launch (a prediction)
-    int pad[8];
+    unsigned int gcount;     // predicted first pass: grid barrier arrivals
+    int pad[7];
 };
 
 enum Phase : int { kPhaseHist = 1, kPhaseSearch = 2, kPhaseBin = 4 };
@@ -148,6 +149,53 @@ struct ClusterArgs {
 cudaError_t slice_cluster_prepare();
 cudaError_t slice_cluster_occupancy(int* max_clusters);
 cudaError_t launch_slice_cluster(const ClusterArgs& a, int nclusters, cudaStream_t s);
+
+// Per-slice 1-D form that reads each voxel once (seg_spec.cu): a predicted
+// threshold per slice from a row subsample, Algorithm 1 in the histogram
+// pass, the voxels near the prediction listed, and corrected after the
+// exact search.
+struct SpecArgs {
+    const int16_t* vol;     // [nz][slice_vox], 16-byte aligned, slice_vox % 8 == 0
+    uint8_t* mask;
+    long long slice_vox;    // S = nx * ny <= kSpecMaxSlice
+    long long nvox;         // nz * S
+    int nx, ny, nz;
+    int nseg;               // slices a block's range can meet (list bookkeeping per block)
+    int wcap;               // list entries a warp can keep (its region of exc)
+    int piece_vox;          // voxels per piece of a second pass (a multiple of 8)
+    int npiece;             // pieces per slice (< 4096)
+    int sub_stride;         // prediction: every sub_stride-th row
+    int win;                // list window: levels (t^ - win, t^ + win], 1 <= win <= kSpecMaxWin
+    int lo, L;
+    float q;
+    int polarity;
+    unsigned int flags;     // TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL, kSpecDebugNoPrediction
+    unsigned long long timeout_ns;
+    ScratchHeader* hdr;     // gcount, b_next, b_tail, done, err, epoch (reset by the last block)
+    int* ghist;             // [nz][kMaxLevels] slice histograms, left zeroed
+    unsigned long long* pred;  // [nz] kPredReady | (t^ + 1), left zeroed
+    int* sflag;             // [nz] bit 0: the slice needs a second pass, left zeroed
+    int* toff;              // [grid][nseg][16] where each warp's list of a part of a slice starts
+    int* tcnt;              // [grid][nseg][16] its length (-1: incomplete)
+    unsigned* exc;          // [grid][16][wcap]: (position in slice << 8) | (level - (t^ - win + 1))
+    unsigned* rbq;          // [nz * npiece] second-pass queue: z << 12 | piece
+    int* t_out;
+    float* phi_out;
+    int* status;
+    const void* df_tables;
+    const float2* ptab;     // optional term table (2^64 (n / ptab_n)^q) for slices of ptab_n voxels
+    long long ptab_n;
+    unsigned* check;
+};
+constexpr long long kSpecMaxSlice = 1ll << 24;   // positions fit 24 bits of a list entry
+constexpr int kSpecMaxWin = 127;                 // levels fit 8 bits
+constexpr int kSpecWarpList = 256;               // list entries one warp holds for a tile
+constexpr int kSpecWarps = 16;                   // streaming warps of a block
+constexpr unsigned kSpecDebugNoPrediction = 1u << 16;   // test hook: prediction jobs publish nothing
+int slice_spec_smem_bytes();
+cudaError_t slice_spec_prepare();
+cudaError_t slice_spec_occupancy(int* blocks_per_sm);
+cudaError_t launch_slice_spec(const SpecArgs& a, int grid, cudaStream_t s);
 
 // Learned threshold proposer (mlp.cu): 256 features -> 256 -> 256 -> 4096.
 constexpr int kMlpIn = 256, kMlpHid = 256, kMlpOut = 4096, kMlpGroup = 16;

@@ -525,6 +525,214 @@ __device__ SearchResult search1d_table(const int32_t* __restrict__ h, int L, flo
     return SearchResult{t_win, phi_win, TSALLIS_OK | TSALLIS_STATUS_RERANKED};
 }
 
+// ------------------------------------------------------------ fast table search
+//
+// The table search (above) for a histogram whose total count N is that of
+// the term table Tp, over the compacted list of its non-empty levels, with
+// the table reads of a thread issued together: the terms Tp[h_i] for the
+// class sums, then the class powers Tp[N_1] and Tp[N_2]. The arithmetic is
+// the table search's: class-1 and (separately) class-2 double-float sums,
+// the objective in double-float with an error bound at every non-empty
+// level with a non-empty class 2, the smallest level on equal values, and
+// FP64 for the levels whose bound reaches the maximum's. Four barriers (six
+// with a re-rank), against the dozen of search1d_block, and no transcendental
+// functions but log2 at q = 1. Scratch (shared memory): sIC[kMaxBins]
+// (level, count) and sW[kMaxBins] (terms).
+template <class Sync>
+__device__ SearchResult search1d_fast(const int32_t* __restrict__ h, int L, float q, const float2* __restrict__ Tp,
+                                      long long N, SearchSmem& sm, int2* __restrict__ sIC, float2* __restrict__ sW,
+                                      const DfTables* __restrict__ T) {
+    const int tid = Sync::tid(), lane = tid & 31, warp = tid >> 5;
+    const bool shannon = (q == 1.0f);
+    // ---- 1. compaction of the non-empty levels
+    const int base = tid * kBinsPerThread;
+    int hv[kBinsPerThread];
+    if (base + kBinsPerThread <= L && ((L & 3) == 0)) {
+        const int4 a0 = __ldcg(reinterpret_cast<const int4*>(h + base));
+        const int4 a1 = __ldcg(reinterpret_cast<const int4*>(h + base) + 1);
+        hv[0] = a0.x; hv[1] = a0.y; hv[2] = a0.z; hv[3] = a0.w; hv[4] = a1.x; hv[5] = a1.y; hv[6] = a1.z; hv[7] = a1.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kBinsPerThread; ++k) hv[k] = base + k < L ? __ldcg(h + base + k) : 0;
+    }
+    int nz = 0;
+#pragma unroll
+    for (int k = 0; k < kBinsPerThread; ++k) nz += hv[k] > 0;
+    int nz_inc = nz;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, nz_inc, d);
+        if (lane >= d) nz_inc += o;
+    }
+    if (lane == 31) sm.red_i[warp] = nz_inc;
+    Sync::sync();   // 1
+    int M = 0, pos = nz_inc - nz;
+#pragma unroll
+    for (int w = 0; w < kSearchWarps; ++w) {
+        const int v = sm.red_i[w];
+        if (w < warp) pos += v;
+        M += v;
+    }
+#pragma unroll
+    for (int k = 0; k < kBinsPerThread; ++k)
+        if (hv[k] > 0) sIC[pos++] = make_int2(base + k, hv[k]);
+    Sync::sync();   // 2
+    if (M < 2) return SearchResult{-1, 0.f, TSALLIS_ERR_NO_VALID_THRESHOLD};
+
+    // ---- 2. this thread's entries (a contiguous run of at most 8), four at
+    // a time: terms gathered together and kept in sW, run sums
+    const int per = (M + kSearchThreads - 1) / kSearchThreads;
+    const int j0 = min(tid * per, M), j1 = min(j0 + per, M);
+    long long c = 0;
+    F2 run{0.f, 0.f};
+    for (int g = j0; g < j1; g += 4) {
+        int cn[4];
+        float2 tw[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cn[u] = g + u < j1 ? sIC[g + u].y : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) tw[u] = cn[u] > 0 ? __ldg(Tp + cn[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (g + u < j1) sW[g + u] = tw[u];
+            c += cn[u];
+            run = f2_add(run, F2{tw[u].x, tw[u].y});
+        }
+    }
+    // exclusive count and term prefix, exclusive term suffix
+    long long ci = c;
+    F2 pi = run, si = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const long long oc = __shfl_up_sync(0xffffffffu, ci, d);
+        const F2 op = shfl_up_f2(pi, d);
+        const F2 os = shfl_down_f2(si, d);
+        if (lane >= d) { ci += oc; pi = f2_add(op, pi); }
+        if (lane + d < 32) si = f2_add(si, os);
+    }
+    if (lane == 31) { sm.cnt_pre[warp] = ci; sm.w_pre[warp] = pi; }
+    if (lane == 0) sm.w_suf[warp] = si;
+    Sync::sync();   // 3
+    long long c_before = __shfl_up_sync(0xffffffffu, ci, 1);
+    F2 w_before = shfl_up_f2(pi, 1);
+    F2 w_after = shfl_down_f2(si, 1);
+    if (lane == 0) { c_before = 0; w_before = F2{0.f, 0.f}; }
+    if (lane == 31) w_after = F2{0.f, 0.f};
+    {
+        F2 pw{0.f, 0.f}, sw{0.f, 0.f};
+        long long cw = 0;
+        for (int w = 0; w < warp; ++w) { cw += sm.cnt_pre[w]; pw = f2_add(pw, sm.w_pre[w]); }
+        for (int w = kSearchWarps - 1; w > warp; --w) sw = f2_add(sm.w_suf[w], sw);
+        c_before += cw;
+        w_before = f2_add(pw, w_before);
+        w_after = f2_add(w_after, sw);
+    }
+    // class-2 sums from the right: sW[j] becomes Q_2 at entry j
+    {
+        F2 rs = w_after;
+        for (int j = j1 - 1; j >= j0; --j) {
+            const float2 w = sW[j];
+            sW[j] = make_float2(rs.hi, rs.lo);
+            rs = f2_add(F2{w.x, w.y}, rs);
+        }
+    }
+
+    // ---- 3. the objective at each entry, left to right (class-1 sums from
+    // the left), terms and class powers gathered two entries at a time;
+    // mode 1 takes the entries whose bound reaches `lower` in FP64 (re-rank)
+    const F2 qm1 = two_sum(q, -1.0f);
+    auto sweep = [&](int mode, float lower, Top& tp, double& bv, int& bi) {
+        F2 qa = w_before;
+        long long na = c_before;
+        for (int g = j0; g < j1; g += 2) {
+            int cn[2];
+            long long nag[2];
+            float2 tw[2], pa[2], pb[2];
+            long long nn = na;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                cn[u] = g + u < j1 ? sIC[g + u].y : 0;
+                nn += cn[u];
+                nag[u] = nn;
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const bool ok = !shannon && cn[u] > 0 && N - nag[u] > 0;
+                tw[u] = cn[u] > 0 ? __ldg(Tp + cn[u]) : make_float2(0.f, 0.f);
+                pa[u] = ok ? __ldg(Tp + nag[u]) : make_float2(1.f, 0.f);
+                pb[u] = ok ? __ldg(Tp + (N - nag[u])) : make_float2(1.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int j = g + u;
+                if (j >= j1) break;
+                qa = f2_add(qa, F2{tw[u].x, tw[u].y});
+                na = nag[u];
+                const long long nb = N - na;
+                if (nb <= 0) continue;
+                const float2 qb2 = sW[j];
+                const F2 QB{qb2.x, qb2.y};
+                F2 phi;
+                float band;
+                double f = 0.0;
+                if (shannon) {
+                    const F2 la = df_log2_count<true>((unsigned)na, T), lb = df_log2_count<true>((unsigned)nb, T);
+                    const F2 sa = df_div(qa, df_from_u32((unsigned)na)), sb = df_div(QB, df_from_u32((unsigned)nb));
+                    phi = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
+                    band = shannon_band_df(la.hi, sa.hi, lb.hi, sb.hi);
+                    if (mode == 1)
+                        f = 0.6931471805599453 * ((df_to_double(la) - df_to_double(qa) / (double)na) +
+                                                  (df_to_double(lb) - df_to_double(QB) / (double)nb));
+                } else {
+                    const F2 ab = df_mul(df_div(qa, F2{pa[u].x, pa[u].y}), df_div(QB, F2{pb[u].x, pb[u].y}));
+                    phi = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), qm1);
+                    band = tsallis_band_df(ab.hi, phi.hi, q);
+                    if (mode == 1)
+                        f = (1.0 - (df_to_double(qa) / ((double)pa[u].x + (double)pa[u].y)) *
+                                       (df_to_double(QB) / ((double)pb[u].x + (double)pb[u].y))) /
+                            ((double)q - 1.0);
+                }
+                const int lev = sIC[j].x;
+                if (mode == 0) tp = top_merge(Top{phi, lev, band, -INFINITY}, tp);
+                else if (phi.hi + band >= lower) argmax_merge(bv, bi, f, lev);
+            }
+        }
+    };
+    Top tp{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
+    double bv = -INFINITY;
+    int bi = -1;
+    sweep(0, 0.f, tp, bv, bi);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) tp = top_merge(tp, shfl_top(tp, d));
+    if (lane == 0) {
+        sm.top_vh[warp] = tp.v.hi;
+        sm.top_vl[warp] = tp.v.lo;
+        sm.top_i[warp] = tp.i;
+        sm.top_band[warp] = tp.band;
+        sm.top_u2[warp] = tp.u2;
+    }
+    Sync::sync();   // 4
+    Top gt{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
+#pragma unroll
+    for (int w = 0; w < kSearchWarps; ++w)
+        gt = top_merge(gt, Top{{sm.top_vh[w], sm.top_vl[w]}, sm.top_i[w], sm.top_band[w], sm.top_u2[w]});
+    if (gt.i < 0) {
+        Sync::sync();
+        return SearchResult{-1, 0.f, TSALLIS_ERR_NO_VALID_THRESHOLD};
+    }
+    if (!(gt.u2 >= gt.v.hi - gt.band)) {
+        Sync::sync();   // sIC / sW / sm may be reused by the caller after this
+        return SearchResult{gt.i, gt.v.hi + gt.v.lo, TSALLIS_OK};
+    }
+    // ---- 4. near ties: FP64 from the same double-float sums and powers
+    sweep(1, gt.v.hi - gt.band, tp, bv, bi);
+    block_argmax_d<Sync>(bv, bi, sm);
+    const int t_win = sm.red_i[0];
+    const float phi_win = (float)sm.red_dv[0];
+    Sync::sync();
+    return SearchResult{t_win, phi_win, TSALLIS_OK | TSALLIS_STATUS_RERANKED};
+}
+
 // ------------------------------------------------------------ window search
 //
 // The exact search started from a window of candidate levels (a proposer's

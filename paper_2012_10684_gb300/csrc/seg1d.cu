@@ -457,7 +457,9 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
     const int tid = threadIdx.x;
     const int epoch = *(volatile int*)&a.hdr->epoch;
 
+    __shared__ DfTables sdf;
     for (int i = tid; i < kMaxBins; i += kBlockThreads) sh[i] = 0;
+    df_stage(&sdf, static_cast<const DfTables*>(a.df_tables), tid, kBlockThreads);
     if (tid == 0) s_exc_n = 0;
     __syncthreads();
 
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
         }
     } else {
         // ================= workers
-        const DfTables* dft = static_cast<const DfTables*>(a.df_tables);
+        const DfTables* dft = &sdf;
         const int hi = a.lo + a.L - 1 > 32767 ? 32767 : a.lo + a.L - 1;
         int* shb = sh - a.lo;   // shb[v] is level v - lo
         const unsigned long long pol_keep = policy_evict_last();
@@ -721,12 +723,15 @@ __global__ void __launch_bounds__(kSearchThreads) k_search1d(const int32_t* __re
                                                              int32_t* __restrict__ status, float* __restrict__ curve,
                                                              const DfTables* __restrict__ dft) {
     __shared__ SearchSmem sm;
+    __shared__ DfTables sdf;
     extern __shared__ int4 smem_search[];
     float2* sT = reinterpret_cast<float2*>(smem_search);
     int2* sIC = reinterpret_cast<int2*>(sT + kMaxBins);
+    df_stage(&sdf, dft, threadIdx.x, blockDim.x);
+    __syncthreads();
     for (long long g = blockIdx.x; g < nh; g += gridDim.x) {
         SearchResult r = search1d_block<BlockSync>(hist + g * L, L, q, curve ? curve + g * (L - 1) : nullptr, sm,
-                                                   sT, sIC, dft);
+                                                   sT, sIC, &sdf);
         if (threadIdx.x == 0) {
             t_out[g] = r.t;
             phi_out[g] = r.phi;
@@ -745,11 +750,14 @@ __global__ void __launch_bounds__(kSearchThreads) k_search1d_window(const int32_
                                                                     const DfTables* __restrict__ dft) {
     __shared__ SearchSmem sm;
     __shared__ WindowSmem ws;
+    __shared__ DfTables sdf;
     extern __shared__ int4 smem_window[];
     float2* sW = reinterpret_cast<float2*>(smem_window);
     float2* sQ = sW + kMaxBins;
+    df_stage(&sdf, dft, threadIdx.x, blockDim.x);
+    __syncthreads();
     for (long long g = blockIdx.x; g < nh; g += gridDim.x) {
-        SearchResult r = search1d_window<BlockSync>(hist + g * L, L, q, cand + g * k, k, sm, ws, sW, sQ, dft);
+        SearchResult r = search1d_window<BlockSync>(hist + g * L, L, q, cand + g * k, k, sm, ws, sW, sQ, &sdf);
         if (threadIdx.x == 0) {
             t_out[g] = r.t;
             phi_out[g] = r.phi;

@@ -297,12 +297,16 @@ __device__ void block_scan(int c, F2 w, bool suffix, ScanSmem& sm, int& c_out, F
 }
 
 __global__ void __launch_bounds__(kS2Threads) k_s2_rows(const S2Args a) {
+    __shared__ DfTables sdf;
+    df_stage(&sdf, a.T, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const DfTables* T = &sdf;
     __shared__ ScanSmem sm;
     const int k = blockIdx.y, i = blockIdx.x, s = threadIdx.x;
     const long long o = s2_off(a, k) + (long long)i * a.L2;
     const int h = s < a.L2 ? __ldg(a.hist + o + s) : 0;
     F2 w{0.f, 0.f};
-    if (h > 0) w = a.q == 1.0f ? df_hlog2h<true>((unsigned)h, a.T) : df_pow_ratio<true>((unsigned)h, F2{kFixedLog2N, 0.f}, a.q, a.T);
+    if (h > 0) w = a.q == 1.0f ? df_hlog2h<true>((unsigned)h, T) : df_pow_ratio<true>((unsigned)h, F2{kFixedLog2N, 0.f}, a.q, T);
     int c;
     F2 ws;
     block_scan(h, w, false, sm, c, ws);
@@ -465,6 +469,10 @@ __device__ Top block_top2(Top tp, TopSmem& sm) {
 // One block per row t: the objective at every (t, s) in double-float, and
 // the row's top.
 __global__ void __launch_bounds__(kS2Threads) k_s2_eval(const S2Args a) {
+    __shared__ DfTables sdf;
+    df_stage(&sdf, a.T, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const DfTables* T = &sdf;
     __shared__ TopSmem sm;
     const int k = blockIdx.y, t = blockIdx.x, s = threadIdx.x;
     const int m = a.L2 - 1;
@@ -474,7 +482,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_eval(const S2Args a) {
     bool ok = false;
     const bool wanted = !a.cellflag || a.cellflag[(long long)k * kCells2d + (t / kCell2d) * 64 + s / kCell2d];
     if (s < m && wanted) {
-        ok = eval_df(quad_sums(a, k, t, s), a.q, a.T, phi, band);
+        ok = eval_df(quad_sums(a, k, t, s), a.q, T, phi, band);
         if (ok) tp = Top{phi, t * m + s, band, -INFINITY};
     }
     if (a.curve && s < m && wanted)
@@ -536,7 +544,7 @@ __device__ __forceinline__ int window_bits(const S2Args& a, int k, int t, int s)
 // Evaluated in double-float like the objective (FP32 instructions; FP64 is
 // slow on this part); -inf when the cell holds no valid pair, +inf when a
 // bound is unbounded.
-__device__ float cell_bound(const S2Args& a, int k, int t0, int t1, int s0, int s1) {
+__device__ float cell_bound(const S2Args& a, const DfTables* __restrict__ T, int k, int t0, int t1, int s0, int s1) {
     const long long o = s2_off(a, k);
     const long long a0 = o + (long long)t0 * a.L2 + s0, a1 = o + (long long)t1 * a.L2 + s1;
     const long long b_big = o + (long long)(t0 + 1) * a.L2 + (s0 + 1), b_small = o + (long long)(t1 + 1) * a.L2 + (s1 + 1);
@@ -545,7 +553,7 @@ __device__ float cell_bound(const S2Args& a, int k, int t0, int t1, int s0, int 
     const float2 qa0f = a.PW[a0], qa1f = a.PW[a1], qb1f = a.SW[b_big], qb0f = a.SW[b_small];
     const F2 qa0{qa0f.x, qa0f.y}, qa1{qa1f.x, qa1f.y}, qb0{qb0f.x, qb0f.y}, qb1{qb1f.x, qb1f.y};
     if (a.q == 1.0f) {
-        const F2 la = df_log2_count<true>((unsigned)na1, a.T), lb = df_log2_count<true>((unsigned)nb1, a.T);
+        const F2 la = df_log2_count<true>((unsigned)na1, T), lb = df_log2_count<true>((unsigned)nb1, T);
         const F2 sa = df_div(qa0, df_from_u32((unsigned)na1)), sb = df_div(qb0, df_from_u32((unsigned)nb1));
         const F2 phi = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
         return phi.hi + phi.lo;
@@ -554,10 +562,10 @@ __device__ float cell_bound(const S2Args& a, int k, int t0, int t1, int s0, int 
     F2 ab;
     if (a.q < 1.0f) {
         if (na0 <= 0 || nb0 <= 0) return INFINITY;
-        const F2 pa = df_pow_ratio<true>((unsigned)na0, LN, a.q, a.T), pb = df_pow_ratio<true>((unsigned)nb0, LN, a.q, a.T);
+        const F2 pa = df_pow_ratio<true>((unsigned)na0, LN, a.q, T), pb = df_pow_ratio<true>((unsigned)nb0, LN, a.q, T);
         ab = df_mul(df_div(qa1, pa), df_div(qb1, pb));
     } else {
-        const F2 pa = df_pow_ratio<true>((unsigned)na1, LN, a.q, a.T), pb = df_pow_ratio<true>((unsigned)nb1, LN, a.q, a.T);
+        const F2 pa = df_pow_ratio<true>((unsigned)na1, LN, a.q, T), pb = df_pow_ratio<true>((unsigned)nb1, LN, a.q, T);
         ab = df_mul(df_div(qa0, pa), df_div(qb0, pb));
     }
     const F2 phi = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), two_sum(a.q, -1.0f));
@@ -573,6 +581,10 @@ constexpr int kWindowParts = kCells2d / kS2Threads;   // blocks per histogram, o
 // (less a margin far above the evaluation's error), 0 otherwise; only
 // flagged cells are evaluated. winfo (zeroed by the caller) counts flag 1.
 __global__ void __launch_bounds__(kS2Threads) k_s2_window(const S2Args a) {
+    __shared__ DfTables sdf;
+    df_stage(&sdf, a.T, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const DfTables* T = &sdf;
     __shared__ unsigned cand_bits[kCells2d / 32];
     __shared__ float wbest[kS2Threads / 32];
     __shared__ int wcount[kS2Threads / 32];
@@ -590,7 +602,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_window(const S2Args a) {
         if (t >= m || s >= m) continue;
         F2 phi;
         float band;
-        if (eval_df(quad_sums(a, k, t, s), a.q, a.T, phi, band)) best = fmaxf(best, phi.hi + phi.lo);
+        if (eval_df(quad_sums(a, k, t, s), a.q, T, phi, band)) best = fmaxf(best, phi.hi + phi.lo);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -606,7 +618,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_window(const S2Args a) {
     if ((cand_bits[c >> 5] >> (c & 31)) & 1u) {
         f = 2;
     } else if (t0 < m && s0 < m) {
-        const float u = cell_bound(a, k, t0, min(t0 + kCell2d - 1, m - 1), s0, min(s0 + kCell2d - 1, m - 1));
+        const float u = cell_bound(a, T, k, t0, min(t0 + kCell2d - 1, m - 1), s0, min(s0 + kCell2d - 1, m - 1));
         if (u >= thr) {
             f = 1;
             searched = 1;
@@ -625,6 +637,10 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_window(const S2Args a) {
 }
 
 __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
+    __shared__ DfTables sdf;
+    df_stage(&sdf, a.T, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const DfTables* T = &sdf;
     __shared__ TopSmem tsm;
     __shared__ RedSmem sm;
     const int k = blockIdx.x, tid = threadIdx.x;
@@ -676,14 +692,14 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
             const Quad u = quad_sums(a, k, t, s);
             F2 phi;
             float band;
-            if (eval_df(u, a.q, a.T, phi, band) && phi.hi + band >= lower && !repeats(u, t, s))
-                argmax_merge(dv, di, eval64(u, a.q, a.T), t * m + s);
+            if (eval_df(u, a.q, T, phi, band) && phi.hi + band >= lower && !repeats(u, t, s))
+                argmax_merge(dv, di, eval64(u, a.q, T), t * m + s);
         }
     }
     red_argmax_d(dv, di, sm);
     if (di < 0) {   // the maximum is inside its own bound; kept as a guard
         di = g.i;
-        dv = eval64(quad_sums(a, k, g.i / m, g.i % m), a.q, a.T);
+        dv = eval64(quad_sums(a, k, g.i / m, g.i % m), a.q, T);
     }
     const int wt = di / m, ws = di - wt * m;
     const Quad uw = quad_sums(a, k, wt, ws);
@@ -698,8 +714,8 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
             if (u.na != uw.na || u.nb != uw.nb) continue;
             F2 phi;
             float band;
-            if (eval_df(u, a.q, a.T, phi, band) && phi.hi + band >= lower && !repeats(u, t, s) &&
-                fabs(eval64(u, a.q, a.T) - dv) <= tol)
+            if (eval_df(u, a.q, T, phi, band) && phi.hi + band >= lower && !repeats(u, t, s) &&
+                fabs(eval64(u, a.q, T) - dv) <= tol)
                 ci = min(ci, t * m + s);
         }
     }

@@ -183,21 +183,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_slice_cluster(const ClusterArgs
     const unsigned LO2 = ((unsigned)a.lo & 0xffffu) * 0x10001u;
     const unsigned HI2 = ((unsigned)hi_v & 0xffffu) * 0x10001u;
     int* histb = hist - a.lo;   // histb[v] is level v - lo
-    const DfTables* T = static_cast<const DfTables*>(a.df_tables);
+    __shared__ DfTables sdf;
+    const DfTables* T = &sdf;
     const bool shannon = a.q == 1.0f;
-    const F2 LN = df_log2_count<false>((unsigned)S, T);   // log2 N, N = S voxels per slice
     const F2 qm1 = two_sum(a.q, -1.0f);                  // q - 1, exact
     const int level = (int)rank * kLevelsPerCta + tid;   // this thread's level in the search
     const unsigned long long pol = policy_evict_first();
     const unsigned buf_s = smem_addr(buf);
 
     for (int i = tid; i < kMaxBins; i += kThreads) hist[i] = 0;
+    df_stage(&sdf, static_cast<const DfTables*>(a.df_tables), tid, kThreads);
     if (tid == 0) {
         for (int c = 0; c < kChunks; ++c) mbar_init(smem_addr(&ctl.mbar[c]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         ctl.err = 0;
     }
     __syncthreads();
+    const F2 LN = df_log2_count<false>((unsigned)S, T);   // log2 N, N = S voxels per slice (after the staging)
     if (rank == 0 && tid == 0) {
         const int z0 = (int)atomicAdd(&a.hdr->h_next, 1u);
         for (unsigned k = 0; k < kClusterCtas; ++k) st_cluster_u32(map_rank(smem_addr(&ctl.zfirst), k), (unsigned)z0);
