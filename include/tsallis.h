@@ -102,13 +102,14 @@ typedef enum {
 /* 2-D form only (two_d = 1, else TSALLIS_ERR_INVALID_ARG): search as the
  * paper's GPU code does (section III, Table 4), one thread per threshold
  * pair (t, s) summing its quadrants directly, O(L2^2) per pair, instead of
- * through summed-area tables. Counts are exact; terms are FP32 with
- * compensated sums and each pair's objective is formed in FP64, so values
- * agree with the default search to about 1e-7 relative; a pair whose value
- * is within that of another distinct partition's may be chosen instead.
- * Same outputs, ties (smallest t, then s) and curve as the default search;
- * no FP64 re-rank (statuses never carry TSALLIS_STATUS_RERANKED). A
- * comparison point: far slower than the default search. */
+ * through summed-area tables. Counts are exact; terms are pairs of floats
+ * summed with compensation, row by row, and the rows in FP64, so each pair's
+ * objective (formed in FP64) carries a bound of about 1e-9 relative; the
+ * pairs whose bounds reach the largest lower bound are evaluated again in
+ * plain FP64 and the largest wins. Same outputs, tie rule (smallest t, then
+ * s) and curve as the default search; statuses never carry
+ * TSALLIS_STATUS_RERANKED. A comparison point: far slower than the default
+ * search. */
 #define TSALLIS_FLAG_BRUTE_FORCE_2D 0x8u
 
 typedef struct {
@@ -171,6 +172,16 @@ tsallis_status tsallis_set_launch_shape(tsallis_ctx* ctx, int32_t tile_vox, int3
  *   TSALLIS_SLICE_KERNEL_PREDICT: the predicted first-pass kernel where it
  *     applies (slices whose voxel count is a multiple of 8 and at most
  *     2^24; topk = 0), else the tile kernel.
+ *   TSALLIS_SLICE_KERNEL_PIPELINE: the pipelined kernel where it applies
+ *     (slices whose voxel count is a multiple of 8; topk = 0), else the tile
+ *     kernel.
+ * The pipelined kernel cuts the slices into chunks (at most 8 a slice, at
+ * least 65536 voxels) taken in slice order; the block that counts a slice's
+ * last chunk runs its search at once, and each block binarises the chunks it
+ * counted as soon as their slices' thresholds are out, a few microseconds
+ * after it read them, so the second read comes from L2. A wait for a
+ * threshold that runs out (TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL: one chunk never
+ * arrives) makes every slice of the call report TSALLIS_ERR_TIMEOUT.
  * The predicted first-pass kernel reads every voxel once in the usual case:
  * a predicted threshold t^ per slice (the exhaustive search, in FP32, of
  * the histogram of every 16th row of the slice; see tsallis_set_prediction)
@@ -193,6 +204,7 @@ tsallis_status tsallis_set_launch_shape(tsallis_ctx* ctx, int32_t tile_vox, int3
 #define TSALLIS_SLICE_KERNEL_TILES 1
 #define TSALLIS_SLICE_KERNEL_CLUSTER 2
 #define TSALLIS_SLICE_KERNEL_PREDICT 3
+#define TSALLIS_SLICE_KERNEL_PIPELINE 4
 tsallis_status tsallis_set_slice_kernel(tsallis_ctx* ctx, int32_t kind);
 
 /*

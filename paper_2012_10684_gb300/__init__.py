@@ -43,7 +43,7 @@ TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL = 0x1
 TSALLIS_FLAG_PREDICT_PROPOSER = 0x2
 TSALLIS_FLAG_PREDICT_SUBSAMPLE = 0x4
 TSALLIS_FLAG_BRUTE_FORCE_2D = 0x8
-SLICE_KERNELS = {"auto": 0, "tiles": 1, "cluster": 2, "predict": 3}
+SLICE_KERNELS = {"auto": 0, "tiles": 1, "cluster": 2, "predict": 3, "pipeline": 4}
 
 PER_SLICE, WHOLE_VOLUME = 0, 1
 MASK_LOW, MASK_HIGH = 0, 1

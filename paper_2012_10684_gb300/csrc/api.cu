@@ -77,6 +77,11 @@ struct tsallis_ctx {
     void* spec_buf = nullptr;       // predicted thresholds, flags, queue, tile counts, lists
     size_t spec_bytes = 0;
     long long spec_nz = 0, spec_ntot = 0, spec_nl = 0, spec_nexc = 0;   // the layout it holds
+    // pipelined per-slice kernel: resident blocks per SM; per-slice counters
+    // and readiness words for up to pipe_nz slices (zeroed when allocated)
+    int pipe_blocks_per_sm = 0;
+    void* pipe_buf = nullptr;
+    long long pipe_nz = 0;
     // term table of the per-slice search (built for one slice size and q)
     float2* ptab = nullptr;
     long long ptab_cap = 0;     // entries allocated
@@ -676,6 +681,73 @@ tsallis_status segment_spec(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, in
     return cuda_status(launch_slice_spec(a, (int)G, stream));
 }
 
+// The pipelined kernel takes per-slice 1-D work whose slices are whole
+// 16-byte words.
+bool use_slice_pipe(const tsallis_ctx* c, const tsallis_params* p, long long slice, long long nz) {
+    if (c->slice_kernel != TSALLIS_SLICE_KERNEL_PIPELINE) return false;
+    return p->mode == TSALLIS_PER_SLICE && !p->two_d && p->topk == 0 && slice % 8 == 0 && nz <= (1 << 28);
+}
+
+// Per-slice counters [nz] (int) and readiness words [nz] (u64), one buffer
+// grown (never shrunk) and zeroed when allocated; the kernel leaves the
+// counters zeroed and tags the readiness words with its launch number.
+tsallis_status ensure_pipe(tsallis_ctx* c, long long nz, int** parts, unsigned long long** ready) {
+    const size_t o_ready = ((size_t)nz * 4 + 255) & ~size_t(255);
+    if (!c->pipe_buf || c->pipe_nz < nz) {
+        if (c->pipe_buf) {
+            if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
+            cudaFree(c->pipe_buf);
+            c->pipe_buf = nullptr;
+            c->pipe_nz = 0;
+        }
+        const size_t bytes = o_ready + (size_t)nz * 8;
+        if (cudaMalloc(&c->pipe_buf, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return TSALLIS_ERR_OOM;
+        }
+        if (cudaMemset(c->pipe_buf, 0, bytes) != cudaSuccess) return TSALLIS_ERR_CUDA;
+        c->pipe_nz = nz;
+    }
+    const size_t o = ((size_t)c->pipe_nz * 4 + 255) & ~size_t(255);
+    *parts = static_cast<int*>(c->pipe_buf);
+    *ready = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->pipe_buf) + o);
+    return TSALLIS_OK;
+}
+
+tsallis_status segment_pipe(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, int64_t ny, int64_t nz,
+                            const tsallis_params* p, uint8_t* d_mask, int32_t* d_t, float* d_phi, int32_t* d_status,
+                            cudaStream_t stream) {
+    const long long S = nx * ny;
+    const long long G = (long long)c->sm_count * c->pipe_blocks_per_sm;
+    tsallis_status st;
+    if ((st = ensure_scratch(c, nz, 0)) != TSALLIS_OK) return st;
+    PipeArgs a;
+    std::memset(&a, 0, sizeof(a));
+    if ((st = ensure_pipe(c, nz, &a.parts, &a.ready)) != TSALLIS_OK) return st;
+    a.vol = d_vol;
+    a.mask = d_mask;
+    a.slice_vox = S;
+    a.chunks_per_slice = pipe_chunks_per_slice(S, &a.chunk_vox);
+    a.nz = (int)nz;
+    a.lo = p->lo;
+    a.L = p->nbins;
+    a.q = p->q;
+    a.polarity = p->polarity;
+    a.flags = p->flags & TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL;
+    a.timeout_ns = c->timeout_ns;
+    ScratchView v = view(c);
+    a.hdr = v.hdr;
+    a.ghist = v.ghist;
+    a.t_out = d_t;
+    a.phi_out = d_phi;
+    a.status = d_status;
+    a.df_tables = c->df_tables;
+    a.ptab = pow_table(c, S, p->q, stream);
+    a.ptab_n = S;
+    a.check = c->check;
+    return cuda_status(launch_slice_pipe(a, (int)G, stream));
+}
+
 }  // namespace
 
 extern "C" {
@@ -749,6 +821,12 @@ tsallis_status tsallis_create(tsallis_ctx** out, int device) {
         delete c;
         return TSALLIS_ERR_CUDA;
     }
+    if (slice_pipe_prepare() != cudaSuccess || slice_pipe_occupancy(&c->pipe_blocks_per_sm) != cudaSuccess ||
+        c->pipe_blocks_per_sm < 1) {
+        cudaGetLastError();
+        delete c;
+        return TSALLIS_ERR_CUDA;
+    }
     if (preproc_prepare() != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -808,6 +886,7 @@ void tsallis_destroy(tsallis_ctx* c) {
         if (c->check) cudaFree(c->check);
         if (c->hp_buf) cudaFree(c->hp_buf);
         if (c->spec_buf) cudaFree(c->spec_buf);
+        if (c->pipe_buf) cudaFree(c->pipe_buf);
         if (c->hp_ready) {
             for (cudaStream_t& h : c->hp_stream) cudaStreamDestroy(h);
             for (cudaEvent_t& e : c->hp_ev) cudaEventDestroy(e);
@@ -833,7 +912,8 @@ tsallis_status tsallis_set_launch_shape(tsallis_ctx* c, int32_t tile_vox, int32_
 
 tsallis_status tsallis_set_slice_kernel(tsallis_ctx* c, int32_t kind) {
     if (!c || (kind != TSALLIS_SLICE_KERNEL_AUTO && kind != TSALLIS_SLICE_KERNEL_TILES &&
-               kind != TSALLIS_SLICE_KERNEL_CLUSTER && kind != TSALLIS_SLICE_KERNEL_PREDICT))
+               kind != TSALLIS_SLICE_KERNEL_CLUSTER && kind != TSALLIS_SLICE_KERNEL_PREDICT &&
+               kind != TSALLIS_SLICE_KERNEL_PIPELINE))
         return TSALLIS_ERR_INVALID_ARG;
     if (kind == TSALLIS_SLICE_KERNEL_CLUSTER && c->cluster_max < 1) return TSALLIS_ERR_UNIMPLEMENTED;
     c->slice_kernel = kind;
@@ -980,6 +1060,8 @@ tsallis_status tsallis_segment(tsallis_ctx* c, const int16_t* d_vol, int64_t nx,
         const tsallis_volume v{d_vol, d_mask, nx, ny, nz};
         return tsallis_segment_batch(c, &v, 1, p, d_t, d_phi, d_status, stream);
     }
+    if (use_slice_pipe(c, p, slice, nz))
+        return segment_pipe(c, d_vol, nx, ny, nz, p, d_mask, d_t, d_phi, d_status, stream);
     if (use_slice_spec(c, p, slice, nz))
         return segment_spec(c, d_vol, nx, ny, nz, p, d_mask, d_t, d_phi, d_status, stream);
     if (use_slice_cluster(c, p, slice)) {

@@ -38,6 +38,7 @@ enum CheckSite : unsigned {
     kSiteSpecSlice = 401,     // predicted first pass: job's slice
     kSiteSpecPatch = 402,     // predicted first pass: listed position rewritten
     kSiteSpecQueue = 403,     // predicted first pass: second-pass queue position
+    kSitePipeChunk = 501,     // pipelined per-slice kernel: chunk's slice
 };
 
 }  // namespace tsl

@@ -23,7 +23,9 @@ struct ScratchHeader {
     unsigned long long latest;   // (epoch + 1) << 32 | (t + 1): the threshold found
                                  // most recently in this launch (a prediction)
     unsigned int gcount;     // predicted first pass: grid barrier arrivals
-    int pad[7];
+    int pad0;
+    unsigned long long serial;   // pipelined per-slice kernel: launches so far (readiness tags)
+    int pad[4];
 };
 
 enum Phase : int { kPhaseHist = 1, kPhaseSearch = 2, kPhaseBin = 4 };
@@ -196,6 +198,39 @@ int slice_spec_smem_bytes();
 cudaError_t slice_spec_prepare();
 cudaError_t slice_spec_occupancy(int* blocks_per_sm);
 cudaError_t launch_slice_spec(const SpecArgs& a, int grid, cudaStream_t s);
+
+// Per-slice 1-D form in one pipelined pass (seg_pipe.cu): chunks counted in
+// slice order, each slice searched by the block that counts its last chunk,
+// and each chunk binarised by the block that counted it (from L2).
+struct PipeArgs {
+    const int16_t* vol;     // [nz][slice_vox], 16-byte aligned, slice_vox % 8 == 0
+    uint8_t* mask;
+    long long slice_vox;    // S
+    long long chunk_vox;    // voxels per chunk (a multiple of 8; the last chunk of a slice may be shorter)
+    int chunks_per_slice;   // <= 8
+    int nz;
+    int lo, L;
+    float q;
+    int polarity;
+    unsigned int flags;     // TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL
+    unsigned long long timeout_ns;
+    ScratchHeader* hdr;     // h_next, done, err, serial (restored by the last block)
+    int* ghist;             // [nz][kMaxLevels] slice histograms, left zeroed
+    int* parts;             // [nz] chunks of the slice counted, left zeroed
+    unsigned long long* ready;   // [nz] (serial + 1) << 13 | (t + 1) once the slice is searched
+    int* t_out;
+    float* phi_out;
+    int* status;
+    const void* df_tables;
+    const float2* ptab;     // optional term table (2^64 (n / ptab_n)^q) for slices of ptab_n voxels
+    long long ptab_n;
+    unsigned* check;
+};
+int slice_pipe_smem_bytes();
+cudaError_t slice_pipe_prepare();
+cudaError_t slice_pipe_occupancy(int* blocks_per_sm);
+int pipe_chunks_per_slice(long long slice_vox, long long* chunk_vox);
+cudaError_t launch_slice_pipe(const PipeArgs& a, int grid, cudaStream_t s);
 
 // Learned threshold proposer (mlp.cu): 256 features -> 256 -> 256 -> 4096.
 constexpr int kMlpIn = 256, kMlpHid = 256, kMlpOut = 4096, kMlpGroup = 16;

@@ -1,0 +1,390 @@
+// Per-slice 1-D thresholding in one persistent pass over the volume: the
+// histogram of section II-C, the exhaustive search of the Tsallis objective
+// and Algorithm 1, with each slice read from HBM once and re-read from L2.
+//
+// The volume's slices are cut into chunks (at most 8 per slice, taken in
+// slice order from one global counter). Every block repeats, choosing in
+// this order:
+//   * binarise the oldest chunk it has counted, once that chunk's slice has
+//     its threshold (Algorithm 1; the chunk was read a few microseconds
+//     earlier, so it comes from L2);
+//   * count the next chunk (claimed one chunk ahead, so the claim's latency
+//     is hidden) into its shared-memory histogram, add that to the slice's
+//     histogram in global memory and arrive on the slice's counter. The
+//     block that arrives last runs the slice's search right away (all 512
+//     threads) and publishes the threshold;
+//   * otherwise wait, bounded, for the threshold of its oldest chunk.
+// A block keeps at most kRing chunks it has counted but not binarised, and
+// claims no new chunk while it holds kRing - 2; the oldest of them then lies
+// in a slice all of whose chunks were claimed earlier (a slice has at most 8
+// chunks), and a claimed chunk is always counted before its block waits, so
+// every wait ends. Each wait is also bounded in time: one that runs out sets
+// the launch's error flag, every block stops, and every slice of the call
+// reports TSALLIS_ERR_TIMEOUT (the last block restores the scratch state for
+// the next launch).
+#include <cmath>
+#include <cstdint>
+
+#include "common.cuh"
+#include "dfmath.cuh"
+#include "search1d.cuh"
+#include "checked.cuh"
+#include "kernels.h"
+#include "../../include/tsallis.h"
+
+namespace tsl {
+
+namespace {
+
+constexpr int kThreads = kSearchThreads;      // 512
+constexpr int kBar = 1;                       // named barrier of the block's 512 threads
+constexpr int kRing = 16;                     // counted chunks awaiting their threshold
+constexpr int kMaxChunksPerSlice = 8;
+static_assert(kRing - 2 > kMaxChunksPerSlice, "a full ring spans more than one slice");
+// dynamic shared memory: the block histogram (16 KB) inside the search's
+// (level, count) list (32 KB), then the search's terms (32 KB)
+constexpr int kOffTerms = kMaxBins * 8;
+constexpr int kSmemBytes = kOffTerms + kMaxBins * 8;
+
+using Sync = NamedSync<kBar, 0>;
+
+__device__ __forceinline__ void block_sync() { Sync::sync(); }
+__device__ __forceinline__ unsigned prmt(unsigned a, unsigned b, unsigned s) {
+    unsigned d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(s));
+    return d;
+}
+__device__ __forceinline__ void red_add(int* p, int v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+__device__ __forceinline__ unsigned long long policy(bool last) {
+    unsigned long long p;
+    if (last)
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ld_hint(const void* p, unsigned long long pol) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+
+// A voxel's level as a byte offset into the histogram: 4 clamp(v - lo, 0, L - 1).
+struct Levels {
+    int C0;    // -4 lo
+    int top;   // 4 (L - 1)
+};
+
+__device__ __forceinline__ void count8(const Levels& x, uint4 r, char* shb) {
+    const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int a = (int)prmt(w[j], 0u, 0x9910u), b = ((int)w[j]) >> 16;   // the two int16 values
+        const int oa = min(max(a * 4 + x.C0, 0), x.top), ob = min(max(b * 4 + x.C0, 0), x.top);
+        atomicAdd(reinterpret_cast<int*>(shb + oa), 1);
+        atomicAdd(reinterpret_cast<int*>(shb + ob), 1);
+    }
+}
+
+// Counts n voxels (a multiple of 8) into the block histogram.
+__device__ void count_chunk(const Levels& x, const int16_t* __restrict__ src, int n, char* shb,
+                            unsigned long long pol) {
+    const uint4* v = reinterpret_cast<const uint4*>(src);
+    const int nv = n >> 3, tid = threadIdx.x;
+    constexpr int U = 4;
+    int i0 = 0;
+    for (; i0 + U * kThreads <= nv; i0 += U * kThreads) {
+        uint4 r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) r[u] = ld_hint(v + i0 + u * kThreads + tid, pol);
+#pragma unroll
+        for (int u = 0; u < U; ++u) count8(x, r[u], shb);
+    }
+    for (int i = i0 + tid; i < nv; i += kThreads) count8(x, ld_hint(v + i, pol), shb);
+}
+
+// Algorithm 1 at t over n voxels (a multiple of 8): mask = (level <= t) for
+// polarity low, (level > t) for high; t < 0 (no valid threshold) writes 0.
+__device__ void binarise_chunk(const Levels& x, const int16_t* __restrict__ src, uint8_t* __restrict__ dst, int n,
+                               int t, bool le, unsigned long long pol) {
+    const uint4* v = reinterpret_cast<const uint4*>(src);
+    uint2* d = reinterpret_cast<uint2*>(dst);
+    const int nv = n >> 3, tid = threadIdx.x;
+    if (t < 0) {
+        for (int i = tid; i < nv; i += kThreads) st_stream(d + i, make_uint2(0u, 0u));
+        return;
+    }
+    // bit 15 of o + MT2 (16-bit lanes, o <= 0x3ffc): o >= 4 (t + 1), i.e. level > t
+    const unsigned MT2 = (unsigned)(0x8000 - 4 * (t + 1)) * 0x10001u;
+    const unsigned POL = le ? 0x01010101u : 0u;
+    auto mask8 = [&](uint4 r) {
+        const unsigned w[4] = {r.x, r.y, r.z, r.w};
+        unsigned m[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int a = (int)prmt(w[j], 0u, 0x9910u), b = ((int)w[j]) >> 16;
+            const int oa = min(max(a * 4 + x.C0, 0), x.top), ob = min(max(b * 4 + x.C0, 0), x.top);
+            m[j] = prmt((unsigned)oa, (unsigned)ob, 0x5410u) + MT2;
+        }
+        // selector nibbles 9, b, d, f: the sign bytes of the four 16-bit lanes
+        return make_uint2((prmt(m[0], m[1], 0xFDB9u) & 0x01010101u) ^ POL,
+                          (prmt(m[2], m[3], 0xFDB9u) & 0x01010101u) ^ POL);
+    };
+    constexpr int U = 4;
+    int i0 = 0;
+    for (; i0 + U * kThreads <= nv; i0 += U * kThreads) {
+        uint4 r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) r[u] = ld_hint(v + i0 + u * kThreads + tid, pol);
+#pragma unroll
+        for (int u = 0; u < U; ++u) st_stream(d + i0 + u * kThreads + tid, mask8(r[u]));
+    }
+    for (int i = i0 + tid; i < nv; i += kThreads) st_stream(d + i, mask8(ld_hint(v + i, pol)));
+}
+
+enum Kind : int { kCount = 0, kBinarise = 1, kSearch = 2, kWait = 3, kExit = 4 };
+
+struct PipeSmem {
+    SearchSmem ssm;
+    DfTables df;
+    // thread 0's state
+    unsigned long long tag;       // readiness tag of this launch
+    unsigned long long wait_t0;   // start of the current wait (0: not waiting)
+    int ring[kRing];              // counted chunks awaiting their threshold
+    int rhead, rcount;
+    int exhausted;                // every chunk has been claimed
+    int kind[2], arg[2], arg2[2];   // the decision (alternate slots)
+};
+
+// The slice's search, kept out of line: it needs more registers than the
+// chunk loops, and runs about once per block.
+__device__ __noinline__ SearchResult slice_search(const PipeArgs& a, const int* gh, PipeSmem& ks, int2* sIC,
+                                                  float2* sT) {
+    const long long S = a.slice_vox;
+    return (a.ptab != nullptr && S == a.ptab_n)
+               ? search1d_fast<Sync>(gh, a.L, a.q, a.ptab, S, ks.ssm, sIC, sT, &ks.df)
+               : search1d_block<Sync>(gh, a.L, a.q, nullptr, ks.ssm, sT, sIC, &ks.df);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, 2) k_slice_pipe(const PipeArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    int* hist = reinterpret_cast<int*>(smem);
+    char* shb = reinterpret_cast<char*>(smem);
+    int2* sIC = reinterpret_cast<int2*>(smem);
+    float2* sT = reinterpret_cast<float2*>(smem + kOffTerms);
+    __shared__ PipeSmem ks;
+    const int tid = threadIdx.x;
+    const int nc = a.chunks_per_slice;
+
+    for (int i = tid; i < kMaxBins; i += kThreads) hist[i] = 0;
+    df_stage(&ks.df, static_cast<const DfTables*>(a.df_tables), tid, kThreads);
+    if (tid == 0) {
+        ks.tag = ld_volatile_u64(&a.hdr->serial) + 1;   // this launch's readiness tag
+        ks.wait_t0 = 0;
+        ks.rhead = 0;
+        ks.rcount = 0;
+        ks.exhausted = 0;
+    }
+    // thread 0's results in flight, used at the next decision: a claimed
+    // chunk, the counter value of its last arrival, the oldest counted
+    // chunk's readiness word
+    int claim = -1;
+    int arr_z = -1, arr_old = 0;
+    unsigned long long pf_ready = 0;
+    block_sync();
+
+    for (int it = 0;; ++it) {
+        const int slot = it & 1;
+        if (tid == 0) {
+            const int NC = a.nz * nc;
+            int kind = kWait, arg = 0, arg2 = 0;
+            int rhead = ks.rhead, rcount = ks.rcount;
+            if (*(volatile int*)&a.hdr->err) {
+                kind = kExit;
+            } else if (arr_z >= 0 && arr_old == nc - 1) {
+                kind = kSearch;   // this block counted the slice's last chunk
+                arg = arr_z;
+                arr_z = -1;
+            } else {
+                arr_z = -1;
+                if (rcount > 0 && (pf_ready >> 13) == ks.tag) {
+                    kind = kBinarise;   // the oldest counted chunk's slice has its threshold
+                    arg = ks.ring[rhead];
+                    arg2 = (int)(pf_ready & 0x1fffu) - 1;
+                    rhead = (rhead + 1) % kRing;
+                    --rcount;
+                } else {
+                    if (claim < 0 && !ks.exhausted && rcount < kRing - 2)
+                        claim = (int)min(atomicAdd(&a.hdr->h_next, 1u), (unsigned)NC);
+                    if (claim >= NC) {   // fresh or prefetched: past the last chunk
+                        ks.exhausted = 1;
+                        claim = -1;
+                    }
+                    if (claim >= 0) {
+                        kind = kCount;
+                        arg = claim;
+                        ks.ring[(rhead + rcount) % kRing] = claim;
+                        ++rcount;
+                        claim = -1;
+                        // claim the next chunk now; its number arrives while this one is counted
+                        if (!ks.exhausted && rcount < kRing - 2)
+                            claim = (int)min(atomicAdd(&a.hdr->h_next, 1u), (unsigned)NC);
+                    } else if (rcount == 0) {
+                        kind = ks.exhausted ? kExit : kWait;
+                    }
+                }
+            }
+            if (kind == kWait) {
+                // nothing to do until the oldest chunk's threshold arrives
+                const unsigned long long now = globaltimer_ns();
+                if (ks.wait_t0 == 0) ks.wait_t0 = now;
+                if (now - ks.wait_t0 > a.timeout_ns) {
+                    atomicExch(&a.hdr->err, 1);
+                    kind = kExit;
+                } else {
+                    __nanosleep(256);
+                }
+            } else {
+                ks.wait_t0 = 0;
+            }
+            // the oldest counted chunk's threshold, read now and used at the next decision
+            if (rcount > 0) pf_ready = ld_volatile_u64(&a.ready[ks.ring[rhead] / nc]);
+            ks.rhead = rhead;
+            ks.rcount = rcount;
+            ks.kind[slot] = kind;
+            ks.arg[slot] = arg;
+            ks.arg2[slot] = arg2;
+        }
+        block_sync();
+        const int kind = ks.kind[slot], arg = ks.arg[slot];
+        if (kind == kExit) break;
+        if (kind == kWait) continue;
+
+        if (kind == kCount || kind == kBinarise) {
+            const int z = arg / nc, c = arg - z * nc;
+            const long long off = (long long)z * a.slice_vox + (long long)c * a.chunk_vox;
+            const long long rest = a.slice_vox - (long long)c * a.chunk_vox;
+            const int n = (int)(rest < a.chunk_vox ? rest : a.chunk_vox);
+            const Levels lv{-4 * a.lo, 4 * (a.L - 1)};
+            const bool ok = in_range(z, a.nz, a.check, kSitePipeChunk);
+            if (kind == kBinarise) {
+                if (ok) binarise_chunk(lv, a.vol + off, a.mask + off, n, ks.arg2[slot], a.polarity == 0, policy(false));
+                continue;
+            }
+            if (ok) count_chunk(lv, a.vol + off, n, shb, policy(true));
+            block_sync();   // the block histogram is complete
+            int* gh = a.ghist + (long long)z * kMaxBins;
+            for (int i = tid; i < a.L; i += kThreads) {
+                const int v = hist[i];
+                if (v) {
+                    red_add(&gh[i], v);
+                    hist[i] = 0;
+                }
+            }
+            block_sync();   // every add of the chunk is issued
+            if (tid == 0) {
+                if ((a.flags & TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL) && arg == 0) {
+                    // test hook: the first chunk never arrives
+                } else {
+                    __threadfence();
+                    arr_old = atomicAdd(&a.parts[z], 1);   // looked at in the next decision
+                    arr_z = z;
+                }
+            }
+        } else {   // kSearch: every chunk of slice arg has arrived
+            const int z = arg;
+            __threadfence();
+            int* gh = a.ghist + (long long)z * kMaxBins;
+            const SearchResult r = slice_search(a, gh, ks, sIC, sT);
+            // the slice's histogram is left zeroed, and the block histogram (the search's scratch)
+            for (int i = tid * 4; i < kMaxBins; i += kThreads * 4) *reinterpret_cast<int4*>(gh + i) = make_int4(0, 0, 0, 0);
+            for (int i = tid * 4; i < kMaxBins; i += kThreads * 4) *reinterpret_cast<int4*>(hist + i) = make_int4(0, 0, 0, 0);
+            if (tid == 0) {
+                a.t_out[z] = r.t;
+                a.phi_out[z] = r.phi;
+                a.status[z] = r.status;
+                a.parts[z] = 0;
+                __threadfence();
+                *(volatile unsigned long long*)&a.ready[z] = (ks.tag << 13) | (unsigned long long)(r.t + 1);
+            }
+            block_sync();   // the scratch is free before the block counts again
+        }
+    }
+
+    // exit: the last block restores the scratch state for the next launch
+    __shared__ int last;
+    if (tid == 0) {
+        __threadfence();
+        last = atomicAdd(&a.hdr->done, 1u) == gridDim.x - 1;
+    }
+    block_sync();
+    if (!last) return;
+    __threadfence();
+    const bool failed = *(volatile int*)&a.hdr->err != 0;
+    if (failed) {
+        // slices that never completed keep partial histograms and counters
+        for (long long i = tid; i < (long long)a.nz * kMaxBins; i += kThreads) a.ghist[i] = 0;
+        for (int z = tid; z < a.nz; z += kThreads) {
+            a.parts[z] = 0;
+            a.t_out[z] = -1;
+            a.phi_out[z] = 0.f;
+            a.status[z] = TSALLIS_ERR_TIMEOUT;
+        }
+    }
+    block_sync();
+    if (tid == 0) {
+        __threadfence();
+        a.hdr->h_next = 0;
+        a.hdr->done = 0;
+        a.hdr->err = 0;
+        a.hdr->serial = ks.tag;
+        __threadfence();
+    }
+}
+
+int slice_pipe_smem_bytes() { return kSmemBytes; }
+
+cudaError_t slice_pipe_prepare() {
+    return cudaFuncSetAttribute(k_slice_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, slice_pipe_smem_bytes());
+}
+
+cudaError_t slice_pipe_occupancy(int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_slice_pipe, kThreads,
+                                                         slice_pipe_smem_bytes());
+}
+
+int pipe_chunks_per_slice(long long slice_vox, long long* chunk_vox) {
+    // chunks of at least 65536 voxels, at most kMaxChunksPerSlice per slice
+    long long c = (slice_vox + kMaxChunksPerSlice - 1) / kMaxChunksPerSlice;
+    c = (c + 7) / 8 * 8;
+    if (c < 65536) c = 65536;
+    if (c > slice_vox) c = slice_vox;
+    *chunk_vox = c;
+    return (int)((slice_vox + c - 1) / c);
+}
+
+cudaError_t launch_slice_pipe(const PipeArgs& a, int grid, cudaStream_t s) {
+    // cooperative: every block is resident at once (the waits rely on it)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = slice_pipe_smem_bytes();
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_slice_pipe, a);
+}
+
+}  // namespace tsl
