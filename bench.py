@@ -71,34 +71,41 @@ def _profiled_traffic(nvox):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling in the background."""
+    """nvidia-smi clock / throttle sampling in the background (read-only
+    queries). nvidia-smi writes the log itself (-f), which it flushes line by
+    line; it is stopped with SIGINT so that it closes the file."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, uuid=None):
         self.index = index
+        self.uuid = uuid
         self.proc = None
         self.path = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
+        sel = ("GPU-" + self.uuid) if self.uuid else str(self.index)
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
-                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", sel, "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         self.t0 = time.time()
 
     def stop(self):
         if self.proc is not None:
-            self.proc.terminate()
+            import signal
+            time.sleep(0.25)   # at least one sample after the timed region
+            self.proc.send_signal(signal.SIGINT)
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+                self.proc.wait()
         rows = []
         try:
             for line in open(self.path):
@@ -486,6 +493,127 @@ def preprocess_leg(dev, steps=10, warmup=3, nz=NZ):
             "steps": steps}
 
 
+def _timed(dev, fn, steps, warmup):
+    """CUDA-event time per call of fn(i), after warm-up."""
+    import torch
+    for i in range(warmup):
+        fn(i)
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        fn(i)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / steps
+
+
+def _hbm(nvox, ms, bytes_per_voxel):
+    peak, kind = _peaks()
+    ach = bytes_per_voxel * nvox / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "bytes_per_voxel": bytes_per_voxel, "peak_source": kind}
+
+
+def copy_bound(dev, h_vol, h_mask, d_vol, d_mask, reps=20):
+    """The rate the host link allows the host-buffer call: plain
+    page-locked copies of the step's bytes (the volume in, the mask out),
+    the two directions overlapped on two streams."""
+    import torch
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def once():
+        with torch.cuda.stream(s1):
+            d_vol.copy_(h_vol, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_mask.copy_(d_mask, non_blocking=True)
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize(dev)
+    ev[0].record(s1)
+    s2.wait_event(ev[0])
+    for _ in range(reps):
+        once()
+    ev[1].record(s2)
+    s1.wait_event(ev[1])
+    ev[2].record(s1)
+    torch.cuda.synchronize(dev)
+    ms = ev[0].elapsed_time(ev[2]) / reps
+    nvox = d_vol.numel()
+    return {"value": nvox / (ms / 1e3), "unit": "voxels/s", "ms_per_step": ms,
+            "h2d_GBps": 2 * nvox / (ms / 1e3) / 1e9, "d2h_GBps": nvox / (ms / 1e3) / 1e9,
+            "method": "cudaMemcpyAsync of the 209.7 MB volume H2D and the 104.9 MB mask D2H, overlapped on two "
+                      "streams, page-locked buffers, %d repetitions" % reps}
+
+
+def per_slice_legs(dev, vols, masks, outs, args, steps=200, warmup=10):
+    """The rest of the 512x512x400 workload (two alternated volumes): per-slice
+    thresholds at q = 0.5 and 1.5, each per-slice kernel at q = 0.8, the
+    two-pass floor (histogram, search and binarise as three calls), whole-
+    volume thresholds at every q, and the single 512x512 slice."""
+    import torch
+
+    import phantom
+    import paper_2012_10684_gb300 as tg
+    nvox = vols[0].numel()
+    res = {}
+
+    def run(p):
+        return lambda i: tg.tsallis_segment(vols[i & 1], p, masks[i & 1], *outs[i & 1])
+    out = {}
+    for q in (0.5, 1.5):
+        ms = _timed(dev, run(tg.tsallis_params(q=q, mode="slice")), steps, warmup)
+        out["q%g" % q] = {"value": nvox / (ms / 1e3), "unit": "voxels/s", "ms": ms, "roofline": _hbm(nvox, ms, 3)}
+    res["per_slice_q"] = out
+    out = {}
+    for kind in ("tiles", "pipeline", "predict"):
+        tg.set_slice_kernel(kind)
+        ms = _timed(dev, run(tg.tsallis_params(q=Q, mode="slice")), steps, warmup)
+        st = outs[0][2]
+        out[kind] = {"value": nvox / (ms / 1e3), "unit": "voxels/s", "ms": ms, "roofline": _hbm(nvox, ms, 3),
+                     "ok": bool(((st & 0xff) == 0).all().item())}
+    tg.set_slice_kernel("auto")
+    res["slice_kernels_q0.8"] = out
+    # the two-pass floor: every slice histogram, the 400 searches, the binarise pass
+    p = tg.tsallis_params(q=Q, mode="slice")
+    hs = [tg.tsallis_histogram(v, p) for v in vols]
+    ts = [tg.tsallis_search(h, p)[0] for h in hs]
+
+    def two_pass(i):
+        k = i & 1
+        tg.tsallis_histogram(vols[k], p, hs[k])
+        t, _, _ = tg.tsallis_search(hs[k], p)
+        tg.tsallis_binarize(vols[k], t, p, masks[k])
+    ms = _timed(dev, two_pass, steps, warmup)
+    res["two_pass"] = {"value": nvox / (ms / 1e3), "unit": "voxels/s", "ms": ms, "calls": 3,
+                       "roofline": _hbm(nvox, ms, 5), "roofline_3B": _hbm(nvox, ms, 3),
+                       "note": "histogram pass, 400 searches, binarise pass from HBM (5 B/voxel of traffic)"}
+    del hs, ts
+    out = {}
+    o1 = [(torch.empty(1, dtype=torch.int32, device=dev), torch.empty(1, dtype=torch.float32, device=dev),
+           torch.empty(1, dtype=torch.int32, device=dev)) for _ in vols]
+    for q in (0.5, 0.8, 1.5):
+        pv = tg.tsallis_params(q=q, mode="volume")
+        ms = _timed(dev, lambda i: tg.tsallis_segment(vols[i & 1], pv, masks[i & 1], *o1[i & 1]), steps, warmup)
+        out["q%g" % q] = {"value": nvox / (ms / 1e3), "unit": "voxels/s", "ms": ms, "roofline": _hbm(nvox, ms, 5),
+                          "t": int(o1[0][0].item())}
+    res["whole_volume"] = out
+    # one 512x512 slice (the single-slice workload): latency of one call
+    sl = phantom.generate_cuda(phantom.slice_phantom(SEED, NX, NY), device=dev)
+    ps = tg.tsallis_params(q=Q, mode="slice")
+    m1 = torch.empty(sl.shape, dtype=torch.uint8, device=dev)
+    r1 = (torch.empty(1, dtype=torch.int32, device=dev), torch.empty(1, dtype=torch.float32, device=dev),
+          torch.empty(1, dtype=torch.int32, device=dev))
+    ms = _timed(dev, lambda i: tg.tsallis_segment(sl, ps, m1, *r1), 2000, 50)
+    res["single_slice"] = {"workload": "one 512x512 phantom slice, q=0.8, 4096 levels", "latency_us": ms * 1e3,
+                           "value": sl.numel() / (ms / 1e3), "unit": "voxels/s", "t": int(r1[0].item()),
+                           "note": "back-to-back calls on one stream; one launch each"}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -494,6 +622,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-volume batch leg")
+    ap.add_argument("--no-legs", action="store_true", help="skip the per-slice / whole-volume / single-slice legs")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batch leg (for profiling; prints the leg's JSON object)")
     ap.add_argument("--batch-nvol", type=int, default=64)
@@ -547,29 +676,35 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec = phantom.chest_volume(SEED, NX, NY, NZ)
-    vol_np = phantom.generate_host(spec)
-    vol = torch.from_numpy(vol_np).to(dev)
+    # two volumes alternated step by step (each larger than L2)
+    vol_np = phantom.generate_host(phantom.chest_volume(SEED, NX, NY, NZ))
+    vols = [torch.from_numpy(vol_np).to(dev), phantom.generate_cuda(phantom.chest_volume(SEED + 1, NX, NY, NZ), device=dev)]
     p = tg.tsallis_params(q=Q, mode="slice")
-    nvox = vol.numel()
-    mask = torch.empty(vol.shape, dtype=torch.uint8, device=dev)
-    t = torch.empty(NZ, dtype=torch.int32, device=dev)
-    phi = torch.empty(NZ, dtype=torch.float32, device=dev)
-    st = torch.empty(NZ, dtype=torch.int32, device=dev)
+    nvox = vols[0].numel()
+    masks = [torch.empty(v.shape, dtype=torch.uint8, device=dev) for v in vols]
+    outs = [(torch.empty(NZ, dtype=torch.int32, device=dev), torch.empty(NZ, dtype=torch.float32, device=dev),
+             torch.empty(NZ, dtype=torch.int32, device=dev)) for _ in vols]
     stream = torch.cuda.current_stream(dev)
 
-    sampler = ClockSampler(local)
+    def step(i):
+        tg.tsallis_segment(vols[i & 1], p, masks[i & 1], *outs[i & 1])
+
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except (AttributeError, RuntimeError):
+        uuid = None
+    sampler = ClockSampler(local, uuid)
     sampler.start()
-    for _ in range(args.warmup):
-        tg.tsallis_segment(vol, p, mask, t, phi, st)
+    for i in range(args.warmup):
+        step(i)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        tg.tsallis_segment(vol, p, mask, t, phi, st)
+    for i in range(args.steps):
+        step(i)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -577,17 +712,15 @@ def main():
     clocks = ClockSampler.summarise(sampler.stop())
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ms, world, dev)
-    status = st.cpu().numpy()
+    status = np.concatenate([o[2].cpu().numpy() for o in outs])
     assert np.all((status & 0xff) == 0), "a slice failed: %s" % status[(status & 0xff) != 0][:5]
 
-    # end to end through the public API with host buffers: H2D copy of the
-    # volume from pinned memory, the step, D2H of mask and thresholds
-    k_e2e = max(10, min(args.steps, 300))
     # end to end through the host-buffer entry point: the volume is read from
     # page-locked host memory and the mask, thresholds, values and statuses
     # written back to it, the copies pipelined with the kernels by the call
+    k_e2e = max(10, min(args.steps, 300))
     h_vol = torch.from_numpy(vol_np).pin_memory()
-    h_mask = torch.empty(vol.shape, dtype=torch.uint8).pin_memory()
+    h_mask = torch.empty(vols[0].shape, dtype=torch.uint8).pin_memory()
     h_t = torch.empty(NZ, dtype=torch.int32).pin_memory()
     h_phi = torch.empty(NZ, dtype=torch.float32).pin_memory()
     h_st = torch.empty(NZ, dtype=torch.int32).pin_memory()
@@ -602,6 +735,7 @@ def main():
     f1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = max_over_ranks(f0.elapsed_time(f1), world, dev)
+    copy = copy_bound(dev, h_vol, h_mask, vols[0], masks[0])
 
     if rank != 0:
         if world > 1:
@@ -612,25 +746,30 @@ def main():
     per_launch_s = ms / 1e3 / args.steps
     achieved = BYTES_PER_VOXEL * nvox / per_launch_s / 1e9
     traffic = _profiled_traffic(nvox)
+    e2e_value = world * nvox * k_e2e / (e2e_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ, "q": Q, "mode": "per-slice",
-                   "levels": 4096, "l2": "inputs larger than L2 (210 MB volume + 105 MB mask per step)",
+                   "levels": 4096, "slice_kernel": "auto (persistent tile kernel)",
+                   "l2": "two 210 MB volumes (and their 105 MB masks) alternated step by step, each larger than L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_segment1d",
                      "algorithmic_bytes_per_launch": BYTES_PER_VOXEL * nvox,
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s"},
-        "e2e": {"value": world * nvox * k_e2e / (e2e_ms / 1e3), "unit": "voxels/s",
+        "e2e": {"value": e2e_value, "unit": "voxels/s",
                 "h2d_bytes_per_step": nvox * 2, "d2h_bytes_per_step": nvox + NZ * 12, "steps": k_e2e,
-                "call": "tsallis_segment_host (page-locked host buffers, copies pipelined with the kernels)"},
+                "call": "tsallis_segment_host (page-locked host buffers, copies pipelined with the kernels)",
+                "copy_bound": dict(copy, frac=e2e_value / copy["value"])},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "rerank_slices": int(((status & tg.TSALLIS_STATUS_RERANKED) != 0).sum()),
     }
+    if not args.no_legs:
+        line.update(per_slice_legs(dev, vols, masks, outs, args))
     if not args.no_batch:
         line["two_d"] = two_d_leg(dev)
         line["preprocess"] = preprocess_leg(dev)

@@ -176,7 +176,7 @@ tsallis_status tsallis_set_launch_shape(tsallis_ctx* ctx, int32_t tile_vox, int3
  *     (slices whose voxel count is a multiple of 8; topk = 0), else the tile
  *     kernel.
  * The pipelined kernel cuts the slices into chunks (at most 8 a slice, at
- * least 65536 voxels) taken in slice order; the block that counts a slice's
+ * least 131072 voxels) taken in slice order; the block that counts a slice's
  * last chunk runs its search at once, and each block binarises the chunks it
  * counted as soon as their slices' thresholds are out, a few microseconds
  * after it read them, so the second read comes from L2. A wait for a

@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_slice_pipe(const PipeArgs a) {
     int claim = -1;
     int arr_z = -1, arr_old = 0;
     unsigned long long pf_ready = 0;
+    int pf_err = 0;   // the launch's error flag
     block_sync();
 
     for (int it = 0;; ++it) {
@@ -208,12 +209,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_slice_pipe(const PipeArgs a) {
             const int NC = a.nz * nc;
             int kind = kWait, arg = 0, arg2 = 0;
             int rhead = ks.rhead, rcount = ks.rcount;
-            if (*(volatile int*)&a.hdr->err) {
+            if (pf_err) {
                 kind = kExit;
             } else if (arr_z >= 0 && arr_old == nc - 1) {
                 kind = kSearch;   // this block counted the slice's last chunk
                 arg = arr_z;
                 arr_z = -1;
+                __threadfence();   // the other blocks' adds to the slice's histogram are seen after the barrier
             } else {
                 arr_z = -1;
                 if (rcount > 0 && (pf_ready >> 13) == ks.tag) {
@@ -256,7 +258,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_slice_pipe(const PipeArgs a) {
             } else {
                 ks.wait_t0 = 0;
             }
-            // the oldest counted chunk's threshold, read now and used at the next decision
+            // the error flag and the oldest counted chunk's threshold, read now
+            // and used at the next decision
+            pf_err = *(volatile int*)&a.hdr->err;
             if (rcount > 0) pf_ready = ld_volatile_u64(&a.ready[ks.ring[rhead] / nc]);
             ks.rhead = rhead;
             ks.rcount = rcount;
@@ -302,7 +306,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_slice_pipe(const PipeArgs a) {
             }
         } else {   // kSearch: every chunk of slice arg has arrived
             const int z = arg;
-            __threadfence();
             int* gh = a.ghist + (long long)z * kMaxBins;
             const SearchResult r = slice_search(a, gh, ks, sIC, sT);
             // the slice's histogram is left zeroed, and the block histogram (the search's scratch)
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_slice_pipe(const PipeArgs a) {
                 a.phi_out[z] = r.phi;
                 a.status[z] = r.status;
                 a.parts[z] = 0;
-                __threadfence();
+                // the readiness word carries t itself: nothing else needs ordering before it
                 *(volatile unsigned long long*)&a.ready[z] = (ks.tag << 13) | (unsigned long long)(r.t + 1);
             }
             block_sync();   // the scratch is free before the block counts again
@@ -363,10 +366,12 @@ cudaError_t slice_pipe_occupancy(int* blocks_per_sm) {
 }
 
 int pipe_chunks_per_slice(long long slice_vox, long long* chunk_vox) {
-    // chunks of at least 65536 voxels, at most kMaxChunksPerSlice per slice
+    // chunks of at least 131072 voxels (fewer, longer chunks measured
+    // faster than 32768 or 65536 on 512x512 slices), at most
+    // kMaxChunksPerSlice per slice
     long long c = (slice_vox + kMaxChunksPerSlice - 1) / kMaxChunksPerSlice;
     c = (c + 7) / 8 * 8;
-    if (c < 65536) c = 65536;
+    if (c < 131072) c = 131072;
     if (c > slice_vox) c = slice_vox;
     *chunk_vox = c;
     return (int)((slice_vox + c - 1) / c);
