@@ -79,12 +79,17 @@ typedef enum {
 } tsallis_polarity;
 
 /* Debug flags (tests only). */
-#define TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL 0x1u /* tile and cluster kernels: the first histogram
+#define TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL 0x1u /* tile and cluster kernels (and
+                                                tsallis_segment_static): the first histogram
                                                 tile never reports arrival, so waits on its
                                                 histogram run out and its group reports
                                                 TSALLIS_ERR_TIMEOUT; predicted first-pass kernel:
                                                 one block never arrives at the grid barrier
                                                 after the streaming phase, the barrier's wait
+                                                runs out and every slice of the call reports
+                                                TSALLIS_ERR_TIMEOUT; pipelined kernel: the
+                                                first chunk never arrives on its slice's
+                                                counter, the wait for that slice's threshold
                                                 runs out and every slice of the call reports
                                                 TSALLIS_ERR_TIMEOUT */
 /* tsallis_segment_batch, whole-volume mode: binarise in the histogram pass
@@ -443,7 +448,8 @@ tsallis_status tsallis_autotune_batch(tsallis_ctx* ctx, const tsallis_volume* h_
  * held on every GPU that loads the library until the process exits). Limits
  * that follow from it: at most 512 histograms per call (slices in per-slice
  * mode) and at most 16384 work tiles of 65536 voxels (about 1.07e9 voxels in
- * whole-volume mode); 1-D form only (two_d must be 0). Calls beyond those
+ * whole-volume mode); 1-D form only (two_d must be 0) and exhaustive only
+ * (topk must be 0: there is no proposer without a context). Calls beyond those
  * limits return TSALLIS_ERR_INVALID_ARG before anything is enqueued. Other
  * arguments, outputs and statuses are as for tsallis_segment; the device is
  * the current CUDA device.

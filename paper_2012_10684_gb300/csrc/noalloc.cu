@@ -101,7 +101,7 @@ extern "C" tsallis_status tsallis_segment_static(const int16_t* d_vol, int64_t n
     // arguments, the same rules as tsallis_segment
     if (!p || !(p->q > 0.0f) || !(p->q <= 4.0f) || p->nbins < 2 || p->nbins > kMaxLevels ||
         p->lo < -32768 || p->lo > 32767 || (p->mode != TSALLIS_PER_SLICE && p->mode != TSALLIS_WHOLE_VOLUME) ||
-        (p->polarity != TSALLIS_MASK_LOW && p->polarity != TSALLIS_MASK_HIGH) || p->two_d != 0 || p->topk < 0 ||
+        (p->polarity != TSALLIS_MASK_LOW && p->polarity != TSALLIS_MASK_HIGH) || p->two_d != 0 || p->topk != 0 ||
         (p->flags & ~TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL))
         return TSALLIS_ERR_INVALID_ARG;
     if (nx < 1 || ny < 1 || nz < 0 || nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20)) return TSALLIS_ERR_INVALID_ARG;

@@ -288,14 +288,19 @@ __device__ __forceinline__ void locate(const SegArgs& a, unsigned k, int& g, int
     tile = (int)(k - (unsigned)a.groups[lo].tile_off);
 }
 
-// Binarise queue entries: bits 40..63 the launch tag (epoch + 1, 24 bits),
-// bits 20..39 the group, bits 0..19 the tile. An entry is valid for this
-// launch once its tag matches.
+// Binarise queue entries: bits 40..63 the launch tag (1 + epoch mod
+// 0xffffff: never 0), bits 20..39 the group, bits 0..19 the tile. An entry
+// is valid for this launch once its tag matches. The block that takes an
+// entry clears it, and after a launch whose waits ran out the last block
+// clears the whole queue, so no entry outlives its launch and a tag can
+// never be matched by an entry of an earlier launch, however often the tag
+// wraps.
+__device__ __forceinline__ unsigned bq_tag(int epoch) { return (unsigned)epoch % 0xffffffu + 1u; }
 __device__ __forceinline__ unsigned long long bq_pack(int epoch, int g, int tile) {
-    return ((unsigned long long)((epoch + 1) & 0xffffff) << 40) | ((unsigned long long)g << 20) | (unsigned)tile;
+    return ((unsigned long long)bq_tag(epoch) << 40) | ((unsigned long long)g << 20) | (unsigned)tile;
 }
 __device__ __forceinline__ bool bq_valid(unsigned long long e, int epoch) {
-    return (int)(e >> 40) == ((epoch + 1) & 0xffffff);
+    return (unsigned)(e >> 40) == bq_tag(epoch);
 }
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
     unsigned long long v;
@@ -376,13 +381,21 @@ __device__ Work next_work(const SegArgs& a, int epoch, SchedState& st) {
         if (st.pend >= 0) {
             const unsigned long long e = ld_acquire_u64(&a.bq[st.pend]);
             if (bq_valid(e, epoch)) {
-                if ((int)(e & 0xfffff) == kNoopTile) {   // nothing to re-binarise
+                a.bq[st.pend] = 0ull;   // taken: no later launch can see it
+                const int g = (int)((e >> 20) & 0xfffff), tile = (int)(e & 0xfffff);
+                if (tile == kNoopTile) {   // nothing to re-binarise
+                    st.pend = -1;
+                    continue;
+                }
+                if (g >= a.ngroups || (tile & (kPatchItem - 1)) >= group_tiles(a, g)) {
+                    // not an entry this launch wrote: give it up, the call reports TIMEOUT
+                    atomicExch(&h->err, 1);
                     st.pend = -1;
                     continue;
                 }
                 w.kind = 2;
-                w.group = (int)((e >> 20) & 0xfffff);
-                w.tile = (int)(e & 0xfffff);
+                w.group = g;
+                w.tile = tile;
                 w.t = __ldcg(&a.t_out[w.group]);
                 st.pend = -1;
                 st.b_turn = false;
@@ -704,6 +717,10 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                 for (long long i = tid; i < tot; i += kBlockThreads) a.ghist[i] = 0;
             }
         }
+        // positions given up on a timed-out wait may be published late:
+        // clear the queue so that nothing of this launch outlives it
+        if (err && a.bq)
+            for (unsigned i = tid; i < a.ntotal; i += kBlockThreads) a.bq[i] = 0ull;
         __syncthreads();
         if (tid == 0) {
             a.hdr->h_next = 0;

@@ -254,3 +254,34 @@ def test_trained_proposer_narrows_the_search():
     assert res["trained"][0] >= 0.75, res
     assert res["uninformed"][0] == 0.0
     assert res["trained"][1] < res["uninformed"][1], res
+
+
+def test_training_labels_are_the_oracles():
+    """The proposer's training data: 64 generated volumes (64 x 64 x D, D in
+    [8, 40], the training generator's noise and airway ranges), labelled on
+    the GPU by make_dataset. Each whole-volume histogram must equal the
+    oracle's histogram of the same volume generated on the host, and each
+    label the oracle's threshold of that histogram (oracle.search1d), except
+    where the oracle's top-two gap between partitions is below 1e-9."""
+    from paper_2012_10684_gb300 import proposer
+    seed, n, dmin, dmax, nx = 7, 64, 8, 40, 64
+    hist, _, t, st = proposer.make_dataset(n, seed, dmin, dmax, nx=nx, ny=nx)
+    hist, t, st = hist.cpu().numpy(), t.cpu().numpy(), st.cpu().numpy()
+    rng = np.random.default_rng(seed)
+    checked = 0
+    for i in range(n):
+        # the generator's draws, in make_dataset's order
+        nz = int(rng.integers(dmin, dmax + 1))
+        spec = phantom.chest_volume(seed * 100000 + i, nx, nx, nz, generations=int(rng.integers(4, 9)),
+                                    noise_sd=int(rng.integers(5, 31)), vol_id=i)
+        h_o = oracle.hist1d(phantom.generate_host(spec))
+        assert np.array_equal(hist[i], h_o), i
+        t_o, best, gap, _, _ = oracle.search1d(h_o, float(np.float32(0.8)))
+        if t_o < 0:
+            assert t[i] == -1, i
+            continue
+        assert (st[i] & 0xff) == 0, i
+        if gap >= 1e-9:
+            assert t[i] == t_o, (i, t[i], t_o, gap)
+            checked += 1
+    assert checked >= 60

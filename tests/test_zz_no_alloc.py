@@ -69,6 +69,49 @@ def test_static_entry_matches_context_entry_twice(lib, mode, q):
             assert abs(phi[i] - ref[2][i]) <= PHI_RTOL * max(abs(ref[2][i]), 1.0), (call, i)
         if np.array_equal(t, ref[1]):
             assert np.array_equal(mask, ref[0]), call
+        _check_masks(vol_np, mode, t, mask)
+
+
+def _check_masks(vol_np, mode, t, mask):
+    """Every mask is Algorithm 1 at the returned threshold (the oracle's)."""
+    groups = [vol_np[z] for z in range(vol_np.shape[0])] if mode == "slice" else [vol_np]
+    masks = [mask[z] for z in range(vol_np.shape[0])] if mode == "slice" else [mask]
+    for i, (g, m) in enumerate(zip(groups, masks)):
+        assert np.array_equal(m, oracle.binarize(g, int(t[i]))), i
+
+
+def test_static_entry_skipped_arrival_times_out_then_exact(lib):
+    """The first histogram tile never arrives: its slice's wait (the static
+    entry's fixed 1 s limit) runs out and that slice reports TIMEOUT; the
+    scratch the call leaves is clean, so the next call equals the oracle
+    everywhere, masks included."""
+    vol_np = phantom.generate_host(phantom.chest_volume(2012106856, nz=12))
+    vol = torch.from_numpy(vol_np).cuda()
+    p = tg.tsallis_params(q=0.8, flags=tg.TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL)
+    _, t, _, st = (x.cpu().numpy() for x in _static_call(lib, vol, p))
+    assert (st[0] & 0xff) == tg.TSALLIS_ERR_TIMEOUT and t[0] == -1
+    for call in range(2):
+        mask, t, phi, st = (x.cpu().numpy() for x in _static_call(lib, vol, tg.tsallis_params(q=0.8)))
+        t_o, phi_o, gap_o, _ = oracle.segment1d(vol_np, vol_np.shape[1] * vol_np.shape[2], float(np.float32(0.8)),
+                                                nthreads=8, want_mask=False)
+        assert np.all((st & 0xff) == 0), (call, st)
+        for i in range(len(t)):
+            if gap_o[i] >= GAP:
+                assert t[i] == t_o[i], (call, i)
+            assert abs(phi[i] - phi_o[i]) <= PHI_RTOL * max(abs(phi_o[i]), 1.0), (call, i)
+        _check_masks(vol_np, "slice", t, mask)
+
+
+def test_static_entry_rejects_a_proposer_window(lib):
+    vol = torch.zeros((2, 8, 8), dtype=torch.int16, device="cuda")
+    out = torch.empty(vol.shape, dtype=torch.uint8, device="cuda")
+    t = torch.empty(2, dtype=torch.int32, device="cuda")
+    phi = torch.empty(2, dtype=torch.float32, device="cuda")
+    st = torch.empty(2, dtype=torch.int32, device="cuda")
+    p = tg.tsallis_params(topk=64)
+    rc = lib.tsallis_segment_static(vol.data_ptr(), 8, 8, 2, ctypes.byref(p), out.data_ptr(), t.data_ptr(),
+                                    phi.data_ptr(), st.data_ptr(), None)
+    assert rc == tg.TSALLIS_ERR_INVALID_ARG
 
 
 def test_static_entry_rejects_sizes_beyond_its_scratch(lib):
