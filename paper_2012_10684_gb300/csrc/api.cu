@@ -81,7 +81,7 @@ struct tsallis_ctx {
     // and readiness words for up to pipe_nz slices (zeroed when allocated)
     int pipe_blocks_per_sm = 0;
     void* pipe_buf = nullptr;
-    long long pipe_nz = 0;
+    long long pipe_nz = 0, pipe_nexc = 0;
     // term table of the per-slice search (built for one slice size and q)
     float2* ptab = nullptr;
     long long ptab_cap = 0;     // entries allocated
@@ -685,32 +685,44 @@ tsallis_status segment_spec(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, in
 // 16-byte words.
 bool use_slice_pipe(const tsallis_ctx* c, const tsallis_params* p, long long slice, long long nz) {
     if (c->slice_kernel != TSALLIS_SLICE_KERNEL_PIPELINE) return false;
-    return p->mode == TSALLIS_PER_SLICE && !p->two_d && p->topk == 0 && slice % 8 == 0 && nz <= (1 << 28);
+    return p->mode == TSALLIS_PER_SLICE && !p->two_d && p->topk == 0 && slice % 8 == 0 && slice <= kPipeMaxSlice &&
+           nz <= (1 << 28);
 }
 
-// Per-slice counters [nz] (int) and readiness words [nz] (u64), one buffer
-// grown (never shrunk) and zeroed when allocated; the kernel leaves the
-// counters zeroed and tags the readiness words with its launch number.
-tsallis_status ensure_pipe(tsallis_ctx* c, long long nz, int** parts, unsigned long long** ready) {
-    const size_t o_ready = ((size_t)nz * 4 + 255) & ~size_t(255);
-    if (!c->pipe_buf || c->pipe_nz < nz) {
+// Per-slice counters [nz] (int), readiness words [nz] (u64) and the blocks'
+// list regions [nexc] (u32) in one buffer, grown (never shrunk) and zeroed
+// when allocated; the kernel leaves the counters zeroed, tags the readiness
+// words with its launch number and writes list entries before reading them.
+tsallis_status ensure_pipe(tsallis_ctx* c, long long nz, long long nexc, int** parts, unsigned long long** ready,
+                           unsigned** exc) {
+    auto layout = [](long long n, size_t* o_ready, size_t* o_exc) {
+        *o_ready = ((size_t)n * 4 + 255) & ~size_t(255);
+        *o_exc = (*o_ready + (size_t)n * 8 + 255) & ~size_t(255);
+    };
+    size_t o_ready, o_exc;
+    if (!c->pipe_buf || c->pipe_nz < nz || c->pipe_nexc < nexc) {
         if (c->pipe_buf) {
             if (cudaDeviceSynchronize() != cudaSuccess) return TSALLIS_ERR_CUDA;
             cudaFree(c->pipe_buf);
             c->pipe_buf = nullptr;
             c->pipe_nz = 0;
+            c->pipe_nexc = 0;
         }
-        const size_t bytes = o_ready + (size_t)nz * 8;
+        layout(nz, &o_ready, &o_exc);
+        const size_t bytes = o_exc + (size_t)nexc * 4;
         if (cudaMalloc(&c->pipe_buf, bytes) != cudaSuccess) {
             cudaGetLastError();
             return TSALLIS_ERR_OOM;
         }
         if (cudaMemset(c->pipe_buf, 0, bytes) != cudaSuccess) return TSALLIS_ERR_CUDA;
         c->pipe_nz = nz;
+        c->pipe_nexc = nexc;
     }
-    const size_t o = ((size_t)c->pipe_nz * 4 + 255) & ~size_t(255);
-    *parts = static_cast<int*>(c->pipe_buf);
-    *ready = reinterpret_cast<unsigned long long*>(static_cast<char*>(c->pipe_buf) + o);
+    layout(c->pipe_nz, &o_ready, &o_exc);
+    char* b = static_cast<char*>(c->pipe_buf);
+    *parts = reinterpret_cast<int*>(b);
+    *ready = reinterpret_cast<unsigned long long*>(b + o_ready);
+    *exc = reinterpret_cast<unsigned*>(b + o_exc);
     return TSALLIS_OK;
 }
 
@@ -723,17 +735,21 @@ tsallis_status segment_pipe(tsallis_ctx* c, const int16_t* d_vol, int64_t nx, in
     if ((st = ensure_scratch(c, nz, 0)) != TSALLIS_OK) return st;
     PipeArgs a;
     std::memset(&a, 0, sizeof(a));
-    if ((st = ensure_pipe(c, nz, &a.parts, &a.ready)) != TSALLIS_OK) return st;
+    a.chunks_per_slice = pipe_chunks_per_slice(S, &a.chunk_vox);
+    // a warp lists up to a quarter of the 16-byte groups it counts in a chunk (at least 256)
+    a.wcap = (int)(a.chunk_vox / 8 / kSpecWarps / 4 > kSpecWarpList ? a.chunk_vox / 8 / kSpecWarps / 4 : kSpecWarpList);
+    a.win = c->spec_win;
+    if ((st = ensure_pipe(c, nz, G * kPipeRing * kSpecWarps * a.wcap, &a.parts, &a.ready, &a.exc)) != TSALLIS_OK)
+        return st;
     a.vol = d_vol;
     a.mask = d_mask;
     a.slice_vox = S;
-    a.chunks_per_slice = pipe_chunks_per_slice(S, &a.chunk_vox);
     a.nz = (int)nz;
     a.lo = p->lo;
     a.L = p->nbins;
     a.q = p->q;
     a.polarity = p->polarity;
-    a.flags = p->flags & TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL;
+    a.flags = (p->flags & TSALLIS_FLAG_DEBUG_SKIP_ARRIVAL) | (c->spec_test_flags ? kPipeDebugNoPrediction : 0u);
     a.timeout_ns = c->timeout_ns;
     ScratchView v = view(c);
     a.hdr = v.hdr;

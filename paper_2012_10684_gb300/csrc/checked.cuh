@@ -39,6 +39,7 @@ enum CheckSite : unsigned {
     kSiteSpecPatch = 402,     // predicted first pass: listed position rewritten
     kSiteSpecQueue = 403,     // predicted first pass: second-pass queue position
     kSitePipeChunk = 501,     // pipelined per-slice kernel: chunk's slice
+    kSitePipePatch = 502,     // pipelined per-slice kernel: listed position rewritten
 };
 
 }  // namespace tsl

@@ -25,7 +25,8 @@ struct ScratchHeader {
     unsigned int gcount;     // predicted first pass: grid barrier arrivals
     int pad0;
     unsigned long long serial;   // pipelined per-slice kernel: launches so far (readiness tags)
-    int pad[4];
+    unsigned long long pipe_latest;   // pipelined kernel: (serial + 1) << 13 | (t + 1), the latest threshold
+    int pad[2];
 };
 
 enum Phase : int { kPhaseHist = 1, kPhaseSearch = 2, kPhaseBin = 4 };
@@ -218,6 +219,9 @@ struct PipeArgs {
     int* ghist;             // [nz][kMaxLevels] slice histograms, left zeroed
     int* parts;             // [nz] chunks of the slice counted, left zeroed
     unsigned long long* ready;   // [nz] (serial + 1) << 13 | (t + 1) once the slice is searched
+    int win;                // list window: levels (t^ - win, t^ + win], 1 <= win <= kSpecMaxWin
+    int wcap;               // list entries a warp keeps for one chunk
+    unsigned* exc;          // [grid][kPipeRing][16][wcap]: index in the chunk of a listed 16-byte group
     int* t_out;
     float* phi_out;
     int* status;
@@ -226,6 +230,9 @@ struct PipeArgs {
     long long ptab_n;
     unsigned* check;
 };
+constexpr int kPipeRing = 12;                           // chunks a block counts before finishing them
+constexpr long long kPipeMaxSlice = 1ll << 27;          // 8 chunks of at most 2^24 voxels (list positions)
+constexpr unsigned kPipeDebugNoPrediction = 1u << 16;   // test hook: chunks are counted without a prediction
 int slice_pipe_smem_bytes();
 cudaError_t slice_pipe_prepare();
 cudaError_t slice_pipe_occupancy(int* blocks_per_sm);

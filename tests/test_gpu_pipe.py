@@ -9,9 +9,13 @@ search. The result must be the exhaustive method's, under the rules of the
   * t equal to the oracle's unless the oracle's top-two gap between distinct
     partitions is below 1e-9 relative;
   * |phi_gpu - phi_oracle| <= 1e-5 * max(|phi_oracle|, 1).
-The cases cover chunkings (one chunk a slice, a ragged last chunk, eight
-chunks), thousands of small slices, clamped tails, degenerate slices, a
-threshold that never arrives, and graph replay.
+Each chunk is also binarised in its counting pass at a predicted threshold
+and its voxels near the prediction listed; after the search a chunk is
+left as it is, patched from its lists, or binarised again. The cases drive
+each of those (exact predictions, windows of 1 to 127 levels, lists that
+overflow, no predictions at all) and cover chunkings (one chunk a slice, a
+ragged last chunk, eight chunks), thousands of small slices, clamped
+tails, degenerate slices, a threshold that never arrives, and graph replay.
 """
 import numpy as np
 import pytest
@@ -38,6 +42,8 @@ def _built():
 def _pipeline_kernel():
     tg.set_slice_kernel("pipeline")
     yield
+    tg.set_prediction(16, 8)
+    tg.withhold_predictions(False)
     tg.set_slice_kernel("auto")
 
 
@@ -172,3 +178,30 @@ def test_kernels_agree_on_the_chest_volume():
 def test_full_size_chest_volume(q):
     """The 512x512x400 chest volume in the launch shape the benchmark times."""
     _check(_chest400(), q)
+
+
+@pytest.mark.parametrize("polarity", ["low", "high"])
+@pytest.mark.parametrize("window", [1, 2, 8, 127])
+def test_windows_and_polarity(window, polarity):
+    """A one-level window sends most chunks to a second pass; wide windows
+    list many voxels; both give the exhaustive result."""
+    tg.set_prediction(16, window)
+    v = phantom.generate_host(phantom.chest_volume(2012106857, nz=24))
+    _check(v, 0.8, polarity)
+
+
+def test_list_overflow_falls_back():
+    """Noise concentrated around the threshold (every voxel within the
+    127-level window) overflows the warps' lists (each keeps up to 1/16 of
+    the voxels it counts): those chunks are binarised again, with the same
+    result."""
+    tg.set_prediction(16, 127)
+    rng = np.random.default_rng(9)
+    v = rng.normal(-400, 40, (16, 512, 512)).astype(np.int16)
+    _check(v)
+
+
+def test_without_predictions_every_chunk_is_binarised_again():
+    tg.withhold_predictions(True)
+    v = phantom.generate_host(phantom.chest_volume(2012106858, nz=10))
+    _check(v)

@@ -36,7 +36,7 @@ def _rank_main(rank, world, port, out):
 
 
 def test_max_over_two_gloo_ranks():
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank_main, args=(2, _free_port(), out), nprocs=2, join=True)
     assert dict(out) == {0: 15.0, 1: 15.0}
 
