@@ -46,18 +46,31 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _kernel_source_sha():
+# the sources each per-slice kernel is built from (a profile's traffic figure
+# is used only while they are unchanged)
+KERNEL_SOURCES = {
+    "k_segment1d": ("common.cuh", "dfmath.cuh", "top.cuh", "search1d.cuh", "seg1d.cu", "kernels.h"),
+    "k_slice_pipe": ("common.cuh", "dfmath.cuh", "top.cuh", "search1d.cuh", "firstpass.cuh", "seg_pipe.cu",
+                     "kernels.h"),
+    "k_slice_spec": ("common.cuh", "dfmath.cuh", "top.cuh", "search1d.cuh", "firstpass.cuh", "seg_spec.cu",
+                     "kernels.h"),
+}
+SLICE_KERNEL_NAMES = {"auto": "k_segment1d", "tiles": "k_segment1d", "pipeline": "k_slice_pipe",
+                      "predict": "k_slice_spec"}
+
+
+def _kernel_source_sha(kernel="k_segment1d"):
     h = hashlib.sha256()
-    for name in ("common.cuh", "dfmath.cuh", "top.cuh", "search1d.cuh", "seg1d.cu", "kernels.h"):
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2012_10684_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
 
-def _profiled_traffic(nvox):
+def _profiled_traffic(nvox, kernel="k_segment1d"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_segment1d_chest512x512x400.md")
+    path = os.path.join(ROOT, "profiles", "%s_chest512x512x400.md" % kernel)
     try:
         text = open(path).read()
     except OSError:
@@ -65,7 +78,7 @@ def _profiled_traffic(nvox):
     m_sha = re.search(r"kernel source sha256:\s*([0-9a-f]{64})", text)
     m_b = re.search(r"dram bytes per launch:\s*([0-9.eE+]+)", text)
     m_v = re.search(r"voxels per launch:\s*([0-9]+)", text)
-    if not (m_sha and m_b and m_v) or m_sha.group(1) != _kernel_source_sha():
+    if not (m_sha and m_b and m_v) or m_sha.group(1) != _kernel_source_sha(kernel):
         return None
     return float(m_b.group(1)) * nvox / float(m_v.group(1))
 
@@ -623,6 +636,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-volume batch leg")
     ap.add_argument("--no-legs", action="store_true", help="skip the per-slice / whole-volume / single-slice legs")
+    ap.add_argument("--slice-kernel", default="auto", choices=sorted(SLICE_KERNEL_NAMES),
+                    help="per-slice kernel of the headline step (default: the library's choice)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batch leg (for profiling; prints the leg's JSON object)")
     ap.add_argument("--batch-nvol", type=int, default=64)
@@ -689,6 +704,8 @@ def main():
     def step(i):
         tg.tsallis_segment(vols[i & 1], p, masks[i & 1], *outs[i & 1])
 
+    tg.set_slice_kernel(args.slice_kernel)
+    kernel = SLICE_KERNEL_NAMES[args.slice_kernel]
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
     except (AttributeError, RuntimeError):
@@ -745,18 +762,18 @@ def main():
     peak, peak_kind = _peaks()
     per_launch_s = ms / 1e3 / args.steps
     achieved = BYTES_PER_VOXEL * nvox / per_launch_s / 1e9
-    traffic = _profiled_traffic(nvox)
+    traffic = _profiled_traffic(nvox, kernel)
     e2e_value = world * nvox * k_e2e / (e2e_ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ, "q": Q, "mode": "per-slice",
-                   "levels": 4096, "slice_kernel": "auto (persistent tile kernel)",
+                   "levels": 4096, "slice_kernel": args.slice_kernel + " (" + kernel + ")",
                    "l2": "two 210 MB volumes (and their 105 MB masks) alternated step by step, each larger than L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_segment1d",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
                      "algorithmic_bytes_per_launch": BYTES_PER_VOXEL * nvox,
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s"},
