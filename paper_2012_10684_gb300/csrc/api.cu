@@ -96,6 +96,7 @@ struct tsallis_ctx {
     int prop_sel = 0;
     float* prop_x = nullptr;        // [prop_cap][256]
     int32_t* prop_cand = nullptr;   // [prop_cap][256]
+    unsigned* prop_sync = nullptr;  // barrier words of the fused inference kernel (in prop_x's buffer)
     int prop_cap = 0;
     // first-pass prediction of batches: sub-volume group table, histograms,
     // predicted thresholds and the search's other outputs
@@ -311,14 +312,39 @@ tsallis_status ensure_prop(tsallis_ctx* c, int rows) {
         c->prop_cap = 0;
     }
     void* b = nullptr;
-    if (cudaMalloc(&b, (size_t)rows * (kMlpIn * sizeof(float) + 256 * sizeof(int32_t))) != cudaSuccess) {
+    const size_t main = (size_t)rows * (kMlpIn * sizeof(float) + 256 * sizeof(int32_t));
+    if (cudaMalloc(&b, main + 256) != cudaSuccess) {
         cudaGetLastError();
         return TSALLIS_ERR_OOM;
     }
     c->prop_x = static_cast<float*>(b);
     c->prop_cand = reinterpret_cast<int32_t*>(c->prop_x + (size_t)rows * kMlpIn);
+    c->prop_sync = reinterpret_cast<unsigned*>(static_cast<char*>(b) + main);   // the fused kernel's barrier words
+    if (cudaMemset(c->prop_sync, 0, 256) != cudaSuccess) return TSALLIS_ERR_CUDA;
     c->prop_cap = rows;
     return TSALLIS_OK;
+}
+
+// The proposer's top k of n rows, from histograms (1-D or 2-D features) or
+// from features x: one fused launch for up to kMlpInferRows rows and
+// k <= 64, else the features, forward and top-k kernels. The slot's
+// activations and the context's proposer buffers must hold n rows.
+cudaError_t propose(tsallis_ctx* c, ProposerSlot& S, const int32_t* hist, bool two_d, const float* x, int n, int k,
+                    int32_t* cand, cudaStream_t s) {
+    cudaError_t e;
+    if (hist && two_d) {
+        if ((e = mlp_features2d(hist, n, c->prop_x, s)) != cudaSuccess) return e;
+        hist = nullptr;
+        x = c->prop_x;
+    }
+    if (n <= kMlpInferRows && k <= 64)
+        return mlp_infer(S.mlp, hist, x, c->prop_x, n, k, cand, c->prop_sync, c->timeout_ns, s);
+    if (hist) {
+        if ((e = mlp_features(hist, n, c->prop_x, s)) != cudaSuccess) return e;
+        x = c->prop_x;
+    }
+    if ((e = mlp_forward(S.mlp, x, n, s)) != cudaSuccess) return e;
+    return mlp_topk(S.mlp.z3, n, k, cand, s);
 }
 
 // Window search of nh 1-D histograms: features, proposer, the top k
@@ -334,9 +360,7 @@ tsallis_status search_window(tsallis_ctx* c, const int32_t* d_hist, long long nh
     for (long long h0 = 0; h0 < nh; h0 += chunk) {
         const int n = (int)(nh - h0 < chunk ? nh - h0 : chunk);
         const int32_t* hist = d_hist + h0 * kMlpOut;
-        if (mlp_features(hist, n, c->prop_x, stream) != cudaSuccess ||
-            mlp_forward(S.mlp, c->prop_x, n, stream) != cudaSuccess ||
-            mlp_topk(S.mlp.z3, n, p->topk, c->prop_cand, stream) != cudaSuccess ||
+        if (propose(c, S, hist, false, nullptr, n, p->topk, c->prop_cand, stream) != cudaSuccess ||
             launch_search1d_window(hist, n, kMlpOut, p->q, c->prop_cand, p->topk, d_t + h0, d_phi + h0,
                                    d_status + h0, c->df_tables, stream) != cudaSuccess)
             return TSALLIS_ERR_CUDA;
@@ -473,9 +497,7 @@ cudaError_t search2d_enqueue(tsallis_ctx* c, void* scratch, const int32_t* d_his
             s.cellflag = wbuf;
             s.winfo = reinterpret_cast<int*>(wbuf + align256((size_t)Kmax * kCells2d));
             e = launch_search2d_tables(s, stream);
-            if (e == cudaSuccess) e = mlp_features2d(s.hist, s.K, c->prop_x, stream);
-            if (e == cudaSuccess) e = mlp_forward(c->prop[1].mlp, c->prop_x, (int)s.K, stream);
-            if (e == cudaSuccess) e = mlp_topk(c->prop[1].mlp.z3, (int)s.K, p->topk, c->prop_cand, stream);
+            if (e == cudaSuccess) e = propose(c, c->prop[1], s.hist, true, nullptr, (int)s.K, p->topk, c->prop_cand, stream);
             if (e == cudaSuccess) e = launch_search2d_window(s, stream);
             if (e == cudaSuccess) e = launch_search2d_finish(s, stream);
         } else {
@@ -844,6 +866,11 @@ tsallis_status tsallis_create(tsallis_ctx** out, int device) {
         return TSALLIS_ERR_CUDA;
     }
     if (preproc_prepare() != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return TSALLIS_ERR_CUDA;
+    }
+    if (mlp_prepare() != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return TSALLIS_ERR_CUDA;
@@ -1320,10 +1347,7 @@ tsallis_status tsallis_segment_batch(tsallis_ctx* c, const tsallis_volume* h_vol
             return TSALLIS_ERR_CUDA;
         if (predict & TSALLIS_FLAG_PREDICT_PROPOSER) {
             if ((st = ensure_mlp_act(c, 0, nvol)) != TSALLIS_OK || (st = ensure_prop(c, nvol)) != TSALLIS_OK) return st;
-            if (mlp_features(sh, nvol, c->prop_x, stream) != cudaSuccess ||
-                mlp_forward(S.mlp, c->prop_x, nvol, stream) != cudaSuccess ||
-                mlp_topk(S.mlp.z3, nvol, 1, ht, stream) != cudaSuccess)
-                return TSALLIS_ERR_CUDA;
+            if (propose(c, S, sh, false, nullptr, nvol, 1, ht, stream) != cudaSuccess) return TSALLIS_ERR_CUDA;
         } else if (launch_search1d(sh, nvol, p->nbins, p->q, ht, hphi, hst, nullptr, c->df_tables, stream) !=
                    cudaSuccess) {
             return TSALLIS_ERR_CUDA;
@@ -1564,8 +1588,13 @@ tsallis_status tsallis_proposer_forward(tsallis_ctx* c, const float* d_x, int32_
     DeviceGuard g(c->device);
     if (!g.ok()) return TSALLIS_ERR_CUDA;
     tsallis_status st = ensure_mlp_act(c, c->prop_sel, B);
-    if (st != TSALLIS_OK) return st;
-    if (mlp_forward(S.mlp, d_x, B, stream) != cudaSuccess ||
+    if (st != TSALLIS_OK || (st = ensure_prop(c, B)) != TSALLIS_OK) return st;
+    // up to kMlpInferRows rows: the fused inference kernel (no top k)
+    const cudaError_t e = B <= kMlpInferRows
+                              ? mlp_infer(S.mlp, nullptr, d_x, c->prop_x, B, 0, nullptr, c->prop_sync, c->timeout_ns,
+                                          stream)
+                              : mlp_forward(S.mlp, d_x, B, stream);
+    if (e != cudaSuccess ||
         cudaMemcpyAsync(d_logits, S.mlp.z3, (size_t)B * kMlpOut * sizeof(float), cudaMemcpyDeviceToDevice,
                         stream) != cudaSuccess)
         return TSALLIS_ERR_CUDA;

@@ -264,6 +264,13 @@ cudaError_t mlp_forward(const MlpBuffers& b, const float* x, int B, cudaStream_t
 cudaError_t mlp_backward(const MlpBuffers& b, const float* x, const float* y, int B, float* loss, cudaStream_t s);
 cudaError_t mlp_adam(const MlpBuffers& b, float lr, int step, cudaStream_t s);
 cudaError_t mlp_topk(const float* z, int B, int k, int32_t* out, cudaStream_t s);
+// Inference of up to kMlpInferRows rows in one launch: (hist given) the
+// features into xw, the three layers (logits in b.z3), then (k > 0) the top
+// k of each row into cand. sync: three words, zero between launches.
+constexpr int kMlpInferRows = 64;
+cudaError_t mlp_prepare();
+cudaError_t mlp_infer(const MlpBuffers& b, const int32_t* hist, const float* x, float* xw, int B, int k,
+                      int32_t* cand, unsigned* sync, unsigned long long timeout_ns, cudaStream_t s);
 // Window search (seg1d.cu): nh histograms, k candidate levels each.
 cudaError_t launch_search1d_window(const int32_t* hist, long long nh, int L, float q, const int32_t* cand, int k,
                                    int32_t* t, float* phi, int32_t* status, const void* tables, cudaStream_t s);

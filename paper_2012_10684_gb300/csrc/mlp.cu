@@ -12,10 +12,16 @@
 // FP32. Layout of the flat parameter vector: W1, b1, W2, b2, W3, b3, each
 // matrix row-major [out][in].
 //
-// The products are small (a batch of at most a few thousand rows against
-// 256 x 256 and 4096 x 256 weight matrices), so they run as one tiled
-// shared-memory GEMM on the FP32 pipe with bfloat16 operands widened on
-// load.
+// Every product runs on the tensor cores (mma.sync m16n8k16, bfloat16
+// operands, FP32 accumulation). A bfloat16 operand (the weights) enters as
+// it is; an FP32 operand (features, activations, gradients) is split into a
+// bfloat16 pair hi + lo (hi = rn(v), lo = rn(v - hi), about 16 bits of v)
+// and the product is taken as hi*hi + lo*hi, plus hi*lo when both operands
+// are FP32; the error against the FP32 product of the same operands stays
+// near 2^-16 relative, well inside the tests' tolerances. Training and
+// large batches use one tiled GEMM (k_gemm); inference of up to 64 rows is
+// one cooperative kernel (k_mlp_infer): features, the three layers and the
+// top-k, each weight matrix read once.
 #include <cuda_bf16.h>
 #include <cmath>
 #include <cstdint>
@@ -26,12 +32,38 @@ namespace tsl {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
-constexpr int kGemmThreads = 256;
+constexpr int BM = 64, BN = 64, BK2 = 32;
+constexpr int kGemmThreads = 128;
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// One m16n8k16 product: c += a * b (a: 16 x 16 row-major, b: 16 x 8
+// column-major, bfloat16 pairs; c: 16 x 8 FP32). Fragments (lane = 4 g + t):
+// a[0] (row g, cols 2t, 2t+1), a[1] (row g + 8), a[2] (row g, cols 2t + 8, +9),
+// a[3] (row g + 8, cols 2t + 8, +9); b[0] (rows k = 2t, 2t+1 of col g),
+// b[1] (rows 2t + 8, +9); c[0], c[1] (row g, cols 2t, 2t+1), c[2], c[3]
+// (row g + 8). The lower half of each pair holds the smaller index.
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ unsigned bf16x2_bits(__nv_bfloat162 v) { return *reinterpret_cast<unsigned*>(&v); }
+// Two FP32 values (x the smaller index) as bfloat16 pairs hi and lo.
+__device__ __forceinline__ void split2(float x, float y, unsigned& hi, unsigned& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+    const float2 hf = __bfloat1622float2(h);
+    hi = bf16x2_bits(h);
+    lo = bf16x2_bits(__floats2bfloat162_rn(x - hf.x, y - hf.y));
+}
+__device__ __forceinline__ void split1(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
 // C[M][N] = sum_k A(m, k) B(k, n), then the epilogue.
@@ -40,74 +72,101 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 //         2: B(k, n) = Bf[k * ldb + n]                                  (FP32)
 //   kEpi = 0: C = sum; 1: C = sum + bias[n]; 2: Z = sum + bias[n] and
 //         C = GELU(Z); 3: C += sum (accumulate).
+// A block computes a 64 x 64 tile with 4 warps (32 x 32 each: 2 x 4
+// products of 16 x 8), staging 32-deep slices of both operands in shared
+// memory as bfloat16 hi (and lo) parts, [row][k] with a padded stride.
+constexpr int kTcPad = BK2 + 8;
 template <int kAT, int kBT, int kEpi>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm(int M, int N, int K, const float* __restrict__ A, int lda,
                                                        const __nv_bfloat16* __restrict__ Wb,
                                                        const float* __restrict__ Bf, int ldb,
                                                        const float* __restrict__ bias, float* __restrict__ C,
                                                        float* __restrict__ Z, int ldc) {
-    __shared__ float As[BK][BM + 4];
-    __shared__ float Bs[BK][BN + 4];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    constexpr bool kBsplit = kBT == 2;   // B is FP32: its lo part too
+    __shared__ __align__(16) __nv_bfloat16 Ahi[BM][kTcPad], Alo[BM][kTcPad];
+    __shared__ __align__(16) __nv_bfloat16 Bhi[BN][kTcPad], Blo[kBsplit ? BN : 1][kTcPad];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        // A tile: BM x BK, 4 elements per thread
-        for (int e = threadIdx.x; e < BM * BK; e += kGemmThreads) {
+    float acc[2][4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += BK2) {
+        for (int e = tid; e < BM * BK2; e += kGemmThreads) {
             int mm, kk;
-            if (kAT == 0) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
+            if (kAT == 0) { mm = e / BK2; kk = e % BK2; } else { kk = e / BM; mm = e % BM; }
             const int m = m0 + mm, k = k0 + kk;
             float v = 0.f;
             if (m < M && k < K) v = kAT == 0 ? A[(long long)m * lda + k] : A[(long long)k * lda + m];
-            As[kk][mm] = v;
+            split1(v, Ahi[mm][kk], Alo[mm][kk]);
         }
-        // B tile: BK x BN
-        for (int e = threadIdx.x; e < BK * BN; e += kGemmThreads) {
+        for (int e = tid; e < BK2 * BN; e += kGemmThreads) {
             int kk, nn;
-            if (kBT == 0) { nn = e / BK; kk = e % BK; } else { kk = e / BN; nn = e % BN; }
+            if (kBT == 0) { nn = e / BK2; kk = e % BK2; } else { kk = e / BN; nn = e % BN; }
             const int k = k0 + kk, n = n0 + nn;
-            float v = 0.f;
-            if (k < K && n < N) {
-                if (kBT == 0) v = __bfloat162float(Wb[(long long)n * ldb + k]);
-                else if (kBT == 1) v = __bfloat162float(Wb[(long long)k * ldb + n]);
-                else v = Bf[(long long)k * ldb + n];
+            if (kBsplit) {
+                const float v = (k < K && n < N) ? Bf[(long long)k * ldb + n] : 0.f;
+                split1(v, Bhi[nn][kk], Blo[nn][kk]);
+            } else {
+                __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+                if (k < K && n < N) v = kBT == 0 ? Wb[(long long)n * ldb + k] : Wb[(long long)k * ldb + n];
+                Bhi[nn][kk] = v;
             }
-            Bs[kk][nn] = v;
         }
         __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
-            float a[4], b[4];
+        for (int ks = 0; ks < BK2; ks += 16) {
+            unsigned ah[2][4], al[2][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = wm + mt * 16 + g, c = ks + 2 * t;
+                ah[mt][0] = *reinterpret_cast<const unsigned*>(&Ahi[r][c]);
+                ah[mt][1] = *reinterpret_cast<const unsigned*>(&Ahi[r + 8][c]);
+                ah[mt][2] = *reinterpret_cast<const unsigned*>(&Ahi[r][c + 8]);
+                ah[mt][3] = *reinterpret_cast<const unsigned*>(&Ahi[r + 8][c + 8]);
+                al[mt][0] = *reinterpret_cast<const unsigned*>(&Alo[r][c]);
+                al[mt][1] = *reinterpret_cast<const unsigned*>(&Alo[r + 8][c]);
+                al[mt][2] = *reinterpret_cast<const unsigned*>(&Alo[r][c + 8]);
+                al[mt][3] = *reinterpret_cast<const unsigned*>(&Alo[r + 8][c + 8]);
+            }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+            for (int nt = 0; nt < 4; ++nt) {
+                const int r = wn + nt * 8 + g, c = ks + 2 * t;
+                const unsigned bh[2] = {*reinterpret_cast<const unsigned*>(&Bhi[r][c]),
+                                        *reinterpret_cast<const unsigned*>(&Bhi[r][c + 8])};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma_bf16(acc[mt][nt], ah[mt], bh);
+                    mma_bf16(acc[mt][nt], al[mt], bh);
+                }
+                if (kBsplit) {
+                    const unsigned bl[2] = {*reinterpret_cast<const unsigned*>(&Blo[r][c]),
+                                            *reinterpret_cast<const unsigned*>(&Blo[r][c + 8])};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                    for (int mt = 0; mt < 2; ++mt) mma_bf16(acc[mt][nt], ah[mt], bl);
+                }
+            }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = m0 + ty * 4 + i;
-        if (m >= M) continue;
+    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = n0 + tx * 4 + j;
-            if (n >= N) continue;
-            const long long o = (long long)m * ldc + n;
-            float v = acc[i][j];
-            if (kEpi == 1 || kEpi == 2) v += bias[n];
-            if (kEpi == 2) {
-                Z[o] = v;
-                v = gelu_f(v);
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int m = m0 + wm + mt * 16 + g + (i >> 1) * 8;
+                const int n = n0 + wn + nt * 8 + 2 * t + (i & 1);
+                if (m >= M || n >= N) continue;
+                const long long o = (long long)m * ldc + n;
+                float v = acc[mt][nt][i];
+                if (kEpi == 1 || kEpi == 2) v += bias[n];
+                if (kEpi == 2) {
+                    Z[o] = v;
+                    v = gelu_f(v);
+                }
+                if (kEpi == 3) v += C[o];
+                C[o] = v;
             }
-            if (kEpi == 3) v += C[o];
-            C[o] = v;
-        }
-    }
 }
 
 template <int kAT, int kBT, int kEpi>
@@ -223,11 +282,11 @@ __device__ __forceinline__ void warp_topk_rounds(unsigned long long (&key)[kPer]
         if (lane == 0) out[r] = best;
     }
 }
-__global__ void __launch_bounds__(512) k_topk_small(const float* __restrict__ z, int k, int32_t* __restrict__ out) {
-    __shared__ unsigned long long cand[16 * kTopkSmallMax];   // warp w's k keys at [w * k, w * k + k)
-    __shared__ unsigned long long fin[kTopkSmallMax];
-    const int row = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float* zr = z + (long long)row * kMlpOut;
+// One row by a block of 512 threads (cand: 16 k keys, fin: k keys, in
+// shared memory). Warps other than 0 return after the barrier.
+__device__ void topk_row_small(const float* __restrict__ zr, int k, int32_t* __restrict__ outr,
+                               unsigned long long* cand, unsigned long long* fin) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long key[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -265,31 +324,42 @@ __global__ void __launch_bounds__(512) k_topk_small(const float* __restrict__ z,
         }
         __syncwarp();
     }
-    for (int r = lane; r < k; r += 32)
-        out[(long long)row * k + r] = (int32_t)(0xffffffffu - (unsigned)(fin[r] & 0xffffffffu));
+    for (int r = lane; r < k; r += 32) outr[r] = (int32_t)(0xffffffffu - (unsigned)(fin[r] & 0xffffffffu));
+}
+__global__ void __launch_bounds__(512) k_topk_small(const float* __restrict__ z, int k, int32_t* __restrict__ out) {
+    __shared__ unsigned long long cand[16 * kTopkSmallMax];   // warp w's k keys at [w * k, w * k + k)
+    __shared__ unsigned long long fin[kTopkSmallMax];
+    topk_row_small(z + (long long)blockIdx.x * kMlpOut, k, out + (long long)blockIdx.x * k, cand, fin);
 }
 
-// x[h][k] = log1p(sum of levels 16k..16k+15) / log1p(N); one block per histogram.
+// x[k] = log1p(sum of levels 16k..16k+15) / log1p(N) of one histogram, by
+// the first 256 threads of the block (all threads reach the barriers).
+__device__ void features_row(const int32_t* __restrict__ hrow, float* __restrict__ xrow, long long* part) {
+    const bool on = threadIdx.x < kMlpIn;
+    long long s = 0;
+    if (on) {
+        const int32_t* r = hrow + threadIdx.x * kMlpGroup;
+#pragma unroll
+        for (int j = 0; j < kMlpGroup; ++j) s += r[j];
+    }
+    long long w = s;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+    if (on && (threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = w;
+    __syncthreads();
+    long long n = 0;
+#pragma unroll
+    for (int i = 0; i < kMlpIn / 32; ++i) n += part[i];
+    __syncthreads();
+    const float den = log1pf((float)n);
+    if (on) xrow[threadIdx.x] = n > 0 ? log1pf((float)s) / den : 0.f;
+}
+
+// x[h][k] for nh histograms; one block per histogram.
 __global__ void __launch_bounds__(kMlpIn) k_features(const int32_t* __restrict__ hist, long long nh,
                                                        float* __restrict__ x) {
     __shared__ long long part[kMlpIn / 32];
-    for (long long h = blockIdx.x; h < nh; h += gridDim.x) {
-        const int32_t* r = hist + h * kMlpOut + threadIdx.x * kMlpGroup;
-        long long s = 0;
-#pragma unroll
-        for (int j = 0; j < kMlpGroup; ++j) s += r[j];
-        long long w = s;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
-        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = w;
-        __syncthreads();
-        long long n = 0;
-#pragma unroll
-        for (int i = 0; i < kMlpIn / 32; ++i) n += part[i];
-        __syncthreads();
-        const float den = log1pf((float)n);
-        x[h * kMlpIn + threadIdx.x] = n > 0 ? log1pf((float)s) / den : 0.f;
-    }
+    for (long long h = blockIdx.x; h < nh; h += gridDim.x) features_row(hist + h * kMlpOut, x + h * kMlpIn, part);
 }
 
 // Softmax cross-entropy against soft targets, one block per row: adds the
@@ -430,6 +500,212 @@ __global__ void __launch_bounds__(kMlpIn) k_features2d(const int32_t* __restrict
     }
 }
 
+// ------------------------------------------------------------ fused inference
+//
+// Up to 64 rows in one cooperative launch of kInferBlocks blocks of 512
+// threads, in phases separated by bounded grid barriers:
+//   0. (histograms given) the features of row b, by block b;
+//   1. a1 = GELU(W1 x + b1): block b < 32 owns outputs 8b .. 8b + 7, its warp
+//      w < 4 the rows 16w .. 16w + 15;
+//   2. a2 = GELU(W2 a1 + b2), the same way;
+//   3. z3 = W3 a2 + b3: block b owns outputs 64b .. 64b + 63, its warp w the
+//      outputs 64b + 8 (w mod 8) .. + 7 of rows 16 (w / 8) + 32 q;
+// the layer's input rows are staged in shared memory as bfloat16 hi and lo
+// parts, and each warp loads all of its weight fragments before its first
+// product (so the layer costs one memory latency, not one per k step);
+//   4. (k > 0) the top k of row b, by block b.
+// Each weight matrix is read from memory once. A barrier that runs out of
+// time sets the error word and the kernel runs on: the outputs are then
+// meaningless, but every candidate is still a valid level, which is all the
+// window searches that use them need (their result is certified exact).
+constexpr int kInferBlocks = 64, kInferThreads = 512, kInferRows = 64;
+constexpr int kInferPad = kMlpHid + 8;   // shared-memory row stride of the staged activations (bfloat16)
+constexpr int kInferSmem = 2 * kInferRows * kInferPad * 2;
+
+struct InferArgs {
+    const int32_t* hist;       // [B][4096], or null: x is given
+    const float* x;            // [B][256] features (written by phase 0 when hist is given)
+    float* xw;
+    const __nv_bfloat16* w;    // parameters, bfloat16 (matrices)
+    const float* p32;          // parameters, FP32 (biases)
+    float* a1;                 // [B][256]
+    float* a2;                 // [B][256]
+    float* z3;                 // [B][4096] logits
+    int B, k;
+    int32_t* cand;             // [B][k]
+    unsigned* sync;            // [0] barrier arrivals, [1] blocks done, [2] error
+    unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long infer_clock() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier number `phase` (1, 2, ...): every block arrives once.
+__device__ void infer_barrier(const InferArgs& a, unsigned phase) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&a.sync[0], 1u);
+        const unsigned target = phase * gridDim.x;
+        const unsigned long long t0 = infer_clock();
+        for (unsigned spin = 0;; ++spin) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&a.sync[0]) : "memory");
+            if (v >= target) break;
+            // every 64 polls: the error word and the clock
+            if ((spin & 63u) == 63u) {
+                if (*(volatile unsigned*)&a.sync[2]) break;
+                if (infer_clock() - t0 > a.timeout_ns) {
+                    atomicExch(&a.sync[2], 1u);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Rows 0 .. B-1 of an FP32 [B][256] matrix into shared memory as bfloat16
+// hi and lo parts (stride kInferPad; rows B .. 63 zero), by the whole block.
+__device__ void infer_stage(const float* __restrict__ src, int B, __nv_bfloat16* Shi, __nv_bfloat16* Slo) {
+    constexpr int kPer = kInferRows * (kMlpHid / 2) / kInferThreads;   // 16 pairs a thread, all loads in flight
+    float2 v[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int e = threadIdx.x + j * kInferThreads;
+        const int r = e / (kMlpHid / 2), c2 = (e % (kMlpHid / 2)) * 2;
+        v[j] = r < B ? __ldcg(reinterpret_cast<const float2*>(src + (long long)r * kMlpHid + c2)) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int e = threadIdx.x + j * kInferThreads;
+        const int r = e / (kMlpHid / 2), c2 = (e % (kMlpHid / 2)) * 2;
+        unsigned hi, lo;
+        split2(v[j].x, v[j].y, hi, lo);
+        *reinterpret_cast<unsigned*>(Shi + r * kInferPad + c2) = hi;
+        *reinterpret_cast<unsigned*>(Slo + r * kInferPad + c2) = lo;
+    }
+    __syncthreads();
+}
+
+// One warp: the 8 outputs n0 .. n0 + 7 of (W a)(rows 16 mt + 32 q, q < nq)
+// with the staged rows of a, W bfloat16 [N][256] in global memory. Every
+// weight fragment of the warp is loaded before the first product.
+template <int kQ>
+__device__ __forceinline__ void infer_tile(const __nv_bfloat16* __restrict__ W, int n0, int mt,
+                                           const __nv_bfloat16* Shi, const __nv_bfloat16* Slo, float (&acc)[kQ][4],
+                                           int nq) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const __nv_bfloat16* wr = W + (long long)(n0 + g) * kMlpHid + 2 * t;
+    unsigned bw[kMlpHid / 16][2];
+#pragma unroll
+    for (int k = 0; k < kMlpHid / 16; ++k) {
+        bw[k][0] = __ldg(reinterpret_cast<const unsigned*>(wr + 16 * k));
+        bw[k][1] = __ldg(reinterpret_cast<const unsigned*>(wr + 16 * k + 8));
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[q][i] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMlpHid / 16; ++k) {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            if (q >= nq) break;
+            const int r = 16 * mt + 32 * q + g, c = 16 * k + 2 * t;
+            const unsigned ah[4] = {*reinterpret_cast<const unsigned*>(Shi + r * kInferPad + c),
+                                    *reinterpret_cast<const unsigned*>(Shi + (r + 8) * kInferPad + c),
+                                    *reinterpret_cast<const unsigned*>(Shi + r * kInferPad + c + 8),
+                                    *reinterpret_cast<const unsigned*>(Shi + (r + 8) * kInferPad + c + 8)};
+            const unsigned al[4] = {*reinterpret_cast<const unsigned*>(Slo + r * kInferPad + c),
+                                    *reinterpret_cast<const unsigned*>(Slo + (r + 8) * kInferPad + c),
+                                    *reinterpret_cast<const unsigned*>(Slo + r * kInferPad + c + 8),
+                                    *reinterpret_cast<const unsigned*>(Slo + (r + 8) * kInferPad + c + 8)};
+            mma_bf16(acc[q], ah, bw[k]);
+            mma_bf16(acc[q], al, bw[k]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const InferArgs a) {
+    extern __shared__ __align__(16) unsigned char infer_smem[];
+    __nv_bfloat16* Shi = reinterpret_cast<__nv_bfloat16*>(infer_smem);
+    __nv_bfloat16* Slo = Shi + kInferRows * kInferPad;
+    __shared__ long long part[kMlpIn / 32];
+    __shared__ unsigned long long cand[16 * kTopkSmallMax];
+    __shared__ unsigned long long fin[kTopkSmallMax];
+    const int b = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int B = a.B;
+    unsigned phase = 0;
+    const float* x = a.x;
+    if (a.hist) {
+        if (b < B) features_row(a.hist + (long long)b * kMlpOut, a.xw + (long long)b * kMlpIn, part);
+        infer_barrier(a, ++phase);
+        x = a.xw;
+    }
+    // layers 1 and 2: block b < 32 owns outputs 8b .. 8b + 7; warp w < 4 the
+    // rows 16w .. 16w + 15
+    const bool hid = b < kMlpHid / 8;
+    for (int layer = 0; layer < 2; ++layer) {
+        const float* in = layer == 0 ? x : a.a1;
+        float* out = layer == 0 ? a.a1 : a.a2;
+        if (hid) infer_stage(in, B, Shi, Slo);
+        if (hid && warp < 4 && warp * 16 < B) {
+            float acc[1][4];
+            infer_tile<1>(a.w + (layer == 0 ? kOffW1 : kOffW2), 8 * b, warp, Shi, Slo, acc, 1);
+            const float* bias = a.p32 + (layer == 0 ? kOffB1 : kOffB2);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int row = 16 * warp + g + (i >> 1) * 8, n = 8 * b + 2 * t + (i & 1);
+                if (row < B) out[(long long)row * kMlpHid + n] = gelu_f(acc[0][i] + bias[n]);
+            }
+        }
+        infer_barrier(a, ++phase);
+    }
+    // layer 3: block b owns outputs 64b .. 64b + 63; warp w the outputs
+    // 64b + 8 (w mod 8) .. + 7 of rows 16 (w / 8) + 32 q (q = 0, 1)
+    infer_stage(a.a2, B, Shi, Slo);
+    {
+        const int n0 = 64 * b + 8 * (warp & 7), mt = warp >> 3;
+        const int nq = B > 16 * mt ? ((B - 16 * mt + 31) / 32 < 2 ? (B - 16 * mt + 31) / 32 : 2) : 0;
+        if (nq > 0) {
+            float acc[2][4];
+            infer_tile<2>(a.w + kOffW3, n0, mt, Shi, Slo, acc, nq);
+            const float* b3 = a.p32 + kOffB3;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (q >= nq) break;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int row = 16 * mt + 32 * q + g + (i >> 1) * 8, n = n0 + 2 * t + (i & 1);
+                    if (row < B) a.z3[(long long)row * kMlpOut + n] = acc[q][i] + b3[n];
+                }
+            }
+        }
+    }
+    // the top k of each row
+    if (a.k > 0) {
+        infer_barrier(a, ++phase);
+        if (b < B) topk_row_small(a.z3 + (long long)b * kMlpOut, a.k, a.cand + (long long)b * a.k, cand, fin);
+    }
+    // exit: the last block resets the barrier words for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.sync[1], 1u) == gridDim.x - 1) {
+            a.sync[0] = 0u;
+            a.sync[1] = 0u;
+            a.sync[2] = 0u;
+            __threadfence();
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t mlp_features2d(const int32_t* hist, long long nh, float* x, cudaStream_t s) {
@@ -507,6 +783,42 @@ cudaError_t mlp_topk(const float* z, int B, int k, int32_t* out, cudaStream_t s)
     if (k >= 1 && k <= kTopkSmallMax) k_topk_small<<<B, 512, 0, s>>>(z, k, out);
     else k_topk<<<B, 512, 0, s>>>(z, k, out);
     return cudaGetLastError();
+}
+
+cudaError_t mlp_prepare() {
+    return cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem);
+}
+
+cudaError_t mlp_infer(const MlpBuffers& b, const int32_t* hist, const float* x, float* xw, int B, int k,
+                      int32_t* cand, unsigned* sync, unsigned long long timeout_ns, cudaStream_t s) {
+    if (B < 1 || B > kInferRows || k < 0 || k > kTopkSmallMax || (!hist && !x) || (hist && !xw) || (k > 0 && !cand))
+        return cudaErrorInvalidValue;
+    InferArgs a;
+    a.hist = hist;
+    a.x = x;
+    a.xw = xw;
+    a.w = static_cast<const __nv_bfloat16*>(b.p16);
+    a.p32 = b.p32;
+    a.a1 = b.a1;
+    a.a2 = b.a2;
+    a.z3 = b.z3;
+    a.B = B;
+    a.k = k;
+    a.cand = cand;
+    a.sync = sync;
+    a.timeout_ns = timeout_ns;
+    // cooperative: the grid barriers need every block resident
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kInferBlocks);
+    cfg.blockDim = dim3(kInferThreads);
+    cfg.dynamicSmemBytes = kInferSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_mlp_infer, a);
 }
 
 }  // namespace tsl

@@ -80,6 +80,19 @@ def test_forward_matches_oracle():
     assert np.max(np.abs(z - zo)) <= 1e-4 * (1 + np.max(np.abs(zo)))
 
 
+@pytest.mark.parametrize("B", [1, 16, 17, 64, 65, 300])
+def test_forward_both_paths_match_oracle(B):
+    """Up to 64 rows the fused tensor-core inference kernel, above them the
+    tiled tensor-core GEMMs: both within the forward tolerance of the FP64
+    oracle (bfloat16 weights as used)."""
+    params = _params(21)
+    tg.proposer_set(params)
+    x = np.random.default_rng(B).random((B, 256)).astype(np.float32)
+    z = tg.proposer_forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    zo, _ = mlp.forward(_as_used(params), x)
+    assert np.max(np.abs(z - zo)) <= 1e-4 * (1 + np.max(np.abs(zo))), B
+
+
 def test_gradients_match_oracle():
     params = _params(4)
     tg.proposer_set(params)
