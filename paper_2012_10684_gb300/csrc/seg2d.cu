@@ -49,6 +49,13 @@ namespace {
 
 constexpr int kBand = 32;                  // half-width of the shared-memory band
 constexpr int kBandW = 2 * kBand + 1;
+// Row stride of the band in shared memory: cell (f, d) at f * kBandStride + d
+// lies in bank (4 f + g) mod 32 (g = f + d - kBand; 68 = 4 mod 32), so the
+// cells of a small neighbourhood of (f, g) fall in distinct banks. With the
+// stride kBandW (64 = 0 mod 32) the bank was g mod 32 alone: every voxel of
+// one mean level g collided in one bank whatever its grey level.
+constexpr int kBandStride = 69;
+static_assert(kBandStride >= kBandW && (kBandStride - 1) % 32 == 4, "band stride");
 constexpr int kH2Threads = 512;
 constexpr int kH2RowsPerGroup = 16;        // rows one thread group sweeps per tile
 constexpr int kS2Threads = 256;            // >= L2
@@ -145,19 +152,19 @@ __device__ __forceinline__ void row_sums(const Hist2dArgs& a, int z, int y, int 
 }
 
 // Band-shaped shared histogram: entry (f, g) with d = g - f + kBand in
-// [0, kBandW) lives at band[f * kBandW + d].
+// [0, kBandW) lives at band[f * kBandStride + d].
 __device__ __forceinline__ void count_voxel(int f, int g, int* band, int* gh, int L2) {
     const int d = g - f + kBand;
-    if ((unsigned)d < (unsigned)kBandW) atomicAdd(band + f * kBandW + d, 1);
+    if ((unsigned)d < (unsigned)kBandW) atomicAdd(band + f * kBandStride + d, 1);
     else atomicAdd(gh + f * L2 + g, 1);
 }
 
 __device__ void flush_band(int* band, int* gh, int L2) {
-    const int nb = L2 * kBandW;
+    const int nb = L2 * kBandStride;
     for (int i = threadIdx.x; i < nb; i += kH2Threads) {
         const int c = band[i];
         if (c) {
-            const int f = i / kBandW, g = f + (i - f * kBandW) - kBand;
+            const int f = i / kBandStride, d = i - f * kBandStride, g = f + d - kBand;   // d < kBandW: the pad stays 0
             atomicAdd(gh + f * L2 + g, c);
             band[i] = 0;
         }
@@ -168,7 +175,7 @@ template <int kDz, bool kVec>
 __global__ void __launch_bounds__(kH2Threads, 2) k_hist2d(const Hist2dArgs a) {
     extern __shared__ int band[];
     const int tid = threadIdx.x, lane = tid & 31;
-    for (int i = tid; i < a.L2 * kBandW; i += kH2Threads) band[i] = 0;
+    for (int i = tid; i < a.L2 * kBandStride; i += kH2Threads) band[i] = 0;
     __syncthreads();
     constexpr unsigned kDiv = kDz ? 27u : 9u;
     const unsigned LO2 = ((unsigned)a.lo & 0xffffu) * 0x10001u;
@@ -734,7 +741,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
 
 // ------------------------------------------------------------ host side
 
-int hist2d_smem_bytes(int L2) { return L2 * kBandW * (int)sizeof(int); }
+int hist2d_smem_bytes(int L2) { return L2 * kBandStride * (int)sizeof(int); }
 
 cudaError_t seg2d_prepare() {
     const int smem = hist2d_smem_bytes(256);
