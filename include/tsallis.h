@@ -168,7 +168,10 @@ tsallis_status tsallis_set_launch_shape(tsallis_ctx* ctx, int32_t tile_vox, int3
  * Kernel used by tsallis_segment for per-slice 1-D work (the paper has one
  * GPU design; these are GB300 designs of the same steps, with equal
  * results):
- *   TSALLIS_SLICE_KERNEL_AUTO (default): the persistent tile kernel;
+ *   TSALLIS_SLICE_KERNEL_AUTO (default): the cluster kernel where it applies
+ *     (below) for volumes of at most twice as many slices as 8-CTA
+ *     clusters fit on the device at once (38 on a 152-SM part), else the
+ *     persistent tile kernel;
  *   TSALLIS_SLICE_KERNEL_TILES: the persistent tile kernel;
  *   TSALLIS_SLICE_KERNEL_CLUSTER: the cluster kernel where it applies
  *     (slices of at most 262144 voxels whose voxel count is a multiple of
