@@ -476,27 +476,59 @@ __global__ void __launch_bounds__(512) k_topk(const float* __restrict__ z, int k
 
 // 2-D form: x_f = log1p(count of the 16 x 16 block f of the 256 x 256
 // grey x mean histogram) / log1p(N), f = 16 * (grey block) + mean block.
+// Warp w takes the grey blocks w and w + 8: its lanes read each histogram
+// row as 16-byte words (lane l: columns 8l .. 8l + 7, half of mean block
+// l / 2), eight rows of loads in flight, and lane pairs combine their halves.
+// kVec false: the same with 4-byte loads, for histograms not on a 16-byte
+// boundary.
+template <bool kVec>
 __global__ void __launch_bounds__(kMlpIn) k_features2d(const int32_t* __restrict__ hist, long long nh,
                                                          float* __restrict__ x) {
     __shared__ long long part[kMlpIn / 32];
-    const int bi = threadIdx.x >> 4, bj = threadIdx.x & 15;
+    __shared__ long long blk[256];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (long long h = blockIdx.x; h < nh; h += gridDim.x) {
-        const int32_t* r = hist + h * 65536ll + (bi * 16) * 256 + bj * 16;
-        long long s = 0;
-        for (int i = 0; i < 16; ++i)
+        long long tot = 0;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) s += r[i * 256 + j];
-        long long w = s;
+        for (int q = 0; q < 2; ++q) {
+            const int bi = warp + 8 * q;
+            const int32_t* r = hist + h * 65536ll + (bi * 16) * 256 + 8 * lane;
+            long long s = 0;
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
-        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = w;
+            for (int i0 = 0; i0 < 16; i0 += 8) {
+                int4 v[8][2];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int32_t* e = r + (i0 + i) * 256;
+                    if constexpr (kVec) {
+                        v[i][0] = __ldg(reinterpret_cast<const int4*>(e));
+                        v[i][1] = __ldg(reinterpret_cast<const int4*>(e) + 1);
+                    } else {
+                        v[i][0] = make_int4(__ldg(e), __ldg(e + 1), __ldg(e + 2), __ldg(e + 3));
+                        v[i][1] = make_int4(__ldg(e + 4), __ldg(e + 5), __ldg(e + 6), __ldg(e + 7));
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    s += (long long)v[i][0].x + v[i][0].y + v[i][0].z + v[i][0].w + v[i][1].x + v[i][1].y + v[i][1].z +
+                         v[i][1].w;
+            }
+            s += __shfl_xor_sync(0xffffffffu, s, 1);   // the two halves of mean block lane / 2
+            if ((lane & 1) == 0) blk[bi * 16 + (lane >> 1)] = s;
+            tot += s;
+        }
+        // each block's count appears twice in tot (both lanes of a pair)
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, d);
+        if (lane == 0) part[warp] = tot / 2;
         __syncthreads();
         long long n = 0;
 #pragma unroll
         for (int i = 0; i < kMlpIn / 32; ++i) n += part[i];
+        const long long c = blk[threadIdx.x];
         __syncthreads();
         const float den = log1pf((float)n);
-        x[h * kMlpIn + threadIdx.x] = n > 0 ? log1pf((float)s) / den : 0.f;
+        x[h * kMlpIn + threadIdx.x] = n > 0 ? log1pf((float)c) / den : 0.f;
     }
 }
 
@@ -710,7 +742,11 @@ __global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const InferArgs a) 
 
 cudaError_t mlp_features2d(const int32_t* hist, long long nh, float* x, cudaStream_t s) {
     if (nh <= 0) return cudaSuccess;
-    k_features2d<<<(int)(nh < 65535 ? nh : 65535), kMlpIn, 0, s>>>(hist, nh, x);
+    const int grid = (int)(nh < 65535 ? nh : 65535);
+    if (reinterpret_cast<uintptr_t>(hist) % 16 == 0)
+        k_features2d<true><<<grid, kMlpIn, 0, s>>>(hist, nh, x);
+    else
+        k_features2d<false><<<grid, kMlpIn, 0, s>>>(hist, nh, x);
     return cudaGetLastError();
 }
 

@@ -57,7 +57,14 @@ def test_features2d_match_oracle():
     tg.proposer_select(1)
     h = _hists(11)
     x = tg.proposer_features(h).cpu().numpy()
-    assert np.allclose(x, mlp.features2d(h.cpu().numpy()), rtol=2e-6, atol=2e-7)
+    want = mlp.features2d(h.cpu().numpy())
+    assert np.allclose(x, want, rtol=2e-6, atol=2e-7)
+    # histograms 4 bytes past a 16-byte boundary take the 4-byte-load variant
+    flat = torch.empty(h.numel() + 1, dtype=torch.int32, device=h.device)
+    flat[1:] = h.reshape(-1)
+    hu = flat[1:].view(h.shape)
+    assert hu.data_ptr() % 16 == 4
+    assert np.array_equal(tg.proposer_features(hu).cpu().numpy(), x)
     tg.proposer_select(0)
 
 
