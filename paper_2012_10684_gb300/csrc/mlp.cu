@@ -18,10 +18,11 @@
 // bfloat16 pair hi + lo (hi = rn(v), lo = rn(v - hi), about 16 bits of v)
 // and the product is taken as hi*hi + lo*hi, plus hi*lo when both operands
 // are FP32; the error against the FP32 product of the same operands stays
-// near 2^-16 relative, well inside the tests' tolerances. Training and
-// large batches use one tiled GEMM (k_gemm); inference of up to 64 rows is
-// one cooperative kernel (k_mlp_infer): features, the three layers and the
-// top-k, each weight matrix read once.
+// near 2^-16 relative, well inside the tests' tolerances. Training, batches
+// above 64 rows and windows of more than 64 proposals use one tiled GEMM
+// (k_gemm); inference of up to 64 rows is one cooperative kernel
+// (k_mlp_infer): features, the three layers and the top-k, each weight
+// matrix read once.
 #include <cuda_bf16.h>
 #include <cmath>
 #include <cstdint>
@@ -175,68 +176,6 @@ cudaError_t gemm(int M, int N, int K, const float* A, int lda, const __nv_bfloat
     if (M <= 0 || N <= 0) return cudaSuccess;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     k_gemm<kAT, kBT, kEpi><<<grid, kGemmThreads, 0, s>>>(M, N, K, A, lda, Wb, Bf, ldb, bias, C, Z, ldc);
-    return cudaGetLastError();
-}
-
-// Forward layers for small batches (the searches' proposals: a few to 64
-// rows per launch): C[m][n] = act(sum_k X[m][k] W[n][k] + bias[n]) with
-// K = 256. A block owns 16 outputs of up to 64 rows; thread (m, g) computes
-// outputs n0 + 4g .. n0 + 4g + 3 of row m. The rows' inputs are staged in
-// shared memory 64 columns at a time with a padded stride (the 32 lanes of a
-// warp read 32 rows of one column: distinct banks); the 16 weight rows are
-// read as broadcasts. Epilogue as k_gemm's kEpi 1 (bias) and 2 (bias, Z,
-// GELU).
-constexpr int kSmallRows = 64, kSmallCols = 16, kSmallK = 64;
-template <int kEpi>
-__global__ void __launch_bounds__(256) k_gemm_small(int M, int N, const float* __restrict__ X,
-                                                  const __nv_bfloat16* __restrict__ W,
-                                                  const float* __restrict__ bias, float* __restrict__ C,
-                                                  float* __restrict__ Z) {
-    __shared__ float xs[kSmallRows][kSmallK + 1];
-    __shared__ float ws[kSmallCols][kSmallK];
-    const int m_local = threadIdx.x & (kSmallRows - 1), g = threadIdx.x >> 6;
-    const int m0 = blockIdx.y * kSmallRows, n0 = blockIdx.x * kSmallCols;
-    const int m = m0 + m_local;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k0 = 0; k0 < kMlpIn; k0 += kSmallK) {
-        for (int e = threadIdx.x; e < kSmallRows * kSmallK; e += 256) {
-            const int r = e / kSmallK, kk = e % kSmallK;
-            xs[r][kk] = (m0 + r < M) ? X[(long long)(m0 + r) * kMlpIn + k0 + kk] : 0.f;
-        }
-        for (int e = threadIdx.x; e < kSmallCols * kSmallK; e += 256) {
-            const int c = e / kSmallK, kk = e % kSmallK;
-            ws[c][kk] = (n0 + c < N) ? __bfloat162float(W[(long long)(n0 + c) * kMlpIn + k0 + kk]) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < kSmallK; ++kk) {
-            const float xv = xs[m_local][kk];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[j] = fmaf(xv, ws[g * 4 + j][kk], acc[j]);
-        }
-        __syncthreads();
-    }
-    if (m >= M) return;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int n = n0 + g * 4 + j;
-        if (n >= N) continue;
-        const long long o = (long long)m * N + n;
-        float v = acc[j] + bias[n];
-        if (kEpi == 2) {
-            Z[o] = v;
-            v = gelu_f(v);
-        }
-        C[o] = v;
-    }
-}
-
-template <int kEpi>
-cudaError_t gemm_small(int M, int N, const float* X, const __nv_bfloat16* W, const float* bias, float* C, float* Z,
-                       cudaStream_t s) {
-    if (M <= 0) return cudaSuccess;
-    dim3 grid((N + kSmallCols - 1) / kSmallCols, (M + kSmallRows - 1) / kSmallRows);
-    k_gemm_small<kEpi><<<grid, 256, 0, s>>>(M, N, X, W, bias, C, Z);
     return cudaGetLastError();
 }
 
@@ -764,11 +703,6 @@ cudaError_t mlp_to_bf16(const float* p, void* p16, long long n, cudaStream_t s) 
 cudaError_t mlp_forward(const MlpBuffers& b, const float* x, int B, cudaStream_t s) {
     const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(b.p16);
     cudaError_t e;
-    if (B <= kSmallRows) {
-        if ((e = gemm_small<2>(B, kMlpHid, x, w + kOffW1, b.p32 + kOffB1, b.a1, b.z1, s)) != cudaSuccess) return e;
-        if ((e = gemm_small<2>(B, kMlpHid, b.a1, w + kOffW2, b.p32 + kOffB2, b.a2, b.z2, s)) != cudaSuccess) return e;
-        return gemm_small<1>(B, kMlpOut, b.a2, w + kOffW3, b.p32 + kOffB3, b.z3, nullptr, s);
-    }
     if ((e = gemm<0, 0, 2>(B, kMlpHid, kMlpIn, x, kMlpIn, w + kOffW1, nullptr, kMlpIn, b.p32 + kOffB1, b.a1, b.z1,
                            kMlpHid, s)) != cudaSuccess) return e;
     if ((e = gemm<0, 0, 2>(B, kMlpHid, kMlpHid, b.a1, kMlpHid, w + kOffW2, nullptr, kMlpHid, b.p32 + kOffB2, b.a2,
