@@ -57,6 +57,19 @@ __device__ __forceinline__ bool block_any(bool p, SearchSmem& sm) {
     return r;
 }
 
+// The block's top from the per-warp tops in shared memory (after the barrier
+// that published them), in every warp at once: lane l reads warp l mod 16's
+// top and four xor-shuffle rounds merge them. top_merge only compares and
+// takes maxima, so the result is the serial merge's, bit for bit; a
+// duplicated entry merges with itself unchanged.
+__device__ __forceinline__ Top block_top_of(const SearchSmem& sm) {
+    const int w = threadIdx.x & (kSearchWarps - 1);
+    Top g{{sm.top_vh[w], sm.top_vl[w]}, sm.top_i[w], sm.top_band[w], sm.top_u2[w]};
+#pragma unroll
+    for (int d = kSearchWarps / 2; d > 0; d >>= 1) g = top_merge(g, shfl_top(g, d));
+    return g;
+}
+
 // Block argmax over (value, index) pairs held one per thread; result in
 // sm.red_v[0] / sm.red_i[0] after the call (all threads synchronised).
 template <class Sync>
@@ -466,10 +479,7 @@ __device__ SearchResult search1d_table(const int32_t* __restrict__ h, int L, flo
         sm.top_u2[warp] = tp.u2;
     }
     Sync::sync();
-    Top g{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
-#pragma unroll
-    for (int w = 0; w < kSearchWarps; ++w)
-        g = top_merge(g, Top{{sm.top_vh[w], sm.top_vl[w]}, sm.top_i[w], sm.top_band[w], sm.top_u2[w]});
+    Top g = block_top_of(sm);
     if (g.i < 0) {
         Sync::sync();
         return SearchResult{-1, 0.f, TSALLIS_ERR_NO_VALID_THRESHOLD};
@@ -712,10 +722,7 @@ __device__ SearchResult search1d_fast(const int32_t* __restrict__ h, int L, floa
         sm.top_u2[warp] = tp.u2;
     }
     Sync::sync();   // 4
-    Top gt{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
-#pragma unroll
-    for (int w = 0; w < kSearchWarps; ++w)
-        gt = top_merge(gt, Top{{sm.top_vh[w], sm.top_vl[w]}, sm.top_i[w], sm.top_band[w], sm.top_u2[w]});
+    Top gt = block_top_of(sm);
     if (gt.i < 0) {
         Sync::sync();
         return SearchResult{-1, 0.f, TSALLIS_ERR_NO_VALID_THRESHOLD};
@@ -968,10 +975,7 @@ __device__ SearchResult search1d_window(const int32_t* __restrict__ h, int L, fl
             sm.top_u2[warp] = tp.u2;
         }
         Sync::sync();
-        Top g{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
-#pragma unroll
-        for (int w = 0; w < kSearchWarps; ++w)
-            g = top_merge(g, Top{{sm.top_vh[w], sm.top_vl[w]}, sm.top_i[w], sm.top_band[w], sm.top_u2[w]});
+        Top g = block_top_of(sm);
         Sync::sync();
         return g;
     };
