@@ -347,205 +347,19 @@ __device__ SearchResult search1d_block(const int32_t* __restrict__ h, int L, flo
 
 // ------------------------------------------------------------ table search
 //
-// The same exhaustive search for histograms whose total count N is fixed in
-// advance (one slice of known size), reading the double-float terms
-// 2^64 (n / N)^q for every count n = 0..N from a table (Tp, built once per
-// N and q; at q = 1 the table holds n log2 n). Each thread takes 8
-// consecutive levels; there is no compaction and no FP32 pass: the objective
-// is evaluated in double-float at every non-empty level t with a non-empty
-// class 2 (an empty level gives the same partition as the non-empty level
-// below it, whose value is the smaller t), and the maximum (smallest t on
-// equal values) is taken with a bound on each value's error. Levels whose
-// bound reaches the maximum's are re-ranked in FP64. Scratch: sW and sQ,
-// kMaxBins float2 each (terms and per-thread running sums).
-template <class Sync>
-__device__ SearchResult search1d_table(const int32_t* __restrict__ h, int L, float q, const float2* __restrict__ Tp,
-                                       SearchSmem& sm, float2* __restrict__ sW, float2* __restrict__ sQ,
-                                       const DfTables* __restrict__ T) {
-    const int tid = Sync::tid(), lane = tid & 31, warp = tid >> 5;
-    const bool shannon = (q == 1.0f);
-    const int base = tid * kBinsPerThread;
-
-    // ---- terms of this thread's levels, running sums within the thread
-    int hv[kBinsPerThread];
-    int c = 0;
-#pragma unroll
-    for (int k = 0; k < kBinsPerThread; ++k) {
-        hv[k] = base + k < L ? __ldcg(h + base + k) : 0;
-        c += hv[k];
-    }
-    float2 wv[kBinsPerThread];
-#pragma unroll
-    for (int k = 0; k < kBinsPerThread; ++k) wv[k] = hv[k] > 0 ? __ldg(Tp + hv[k]) : make_float2(0.f, 0.f);
-    F2 run{0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < kBinsPerThread; ++k) {
-        sW[base + k] = wv[k];
-        run = f2_add(run, F2{wv[k].x, wv[k].y});
-        sQ[base + k] = make_float2(run.hi, run.lo);
-    }
-
-    // ---- block scans: exclusive count and term prefix, exclusive term suffix
-    long long ci = c;
-    F2 pi = run, si = run;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const long long oc = __shfl_up_sync(0xffffffffu, ci, d);
-        const F2 op = shfl_up_f2(pi, d);
-        const F2 os = shfl_down_f2(si, d);
-        if (lane >= d) { ci += oc; pi = f2_add(op, pi); }
-        if (lane + d < 32) si = f2_add(si, os);
-    }
-    if (lane == 31) { sm.cnt_pre[warp] = ci; sm.w_pre[warp] = pi; }
-    if (lane == 0) sm.w_suf[warp] = si;
-    Sync::sync();
-    if (warp == 0) {
-        const long long cw = lane < kSearchWarps ? sm.cnt_pre[lane] : 0;
-        long long cc = cw;
-        F2 pp = lane < kSearchWarps ? sm.w_pre[lane] : F2{0.f, 0.f};
-        F2 ss = lane < kSearchWarps ? sm.w_suf[lane] : F2{0.f, 0.f};
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const long long oc = __shfl_up_sync(0xffffffffu, cc, d);
-            const F2 op = shfl_up_f2(pp, d);
-            const F2 os = shfl_down_f2(ss, d);
-            if (lane >= d) { cc += oc; pp = f2_add(op, pp); }
-            if (lane + d < 32) ss = f2_add(ss, os);
-        }
-        F2 pe = shfl_up_f2(pp, 1);
-        if (lane == 0) pe = F2{0.f, 0.f};
-        const F2 se = shfl_down_f2(ss, 1);
-        const long long tot = __shfl_sync(0xffffffffu, cc, kSearchWarps - 1);
-        __syncwarp();
-        if (lane < kSearchWarps) {
-            sm.cnt_pre[lane] = cc - cw;
-            sm.w_pre[lane] = pe;
-            sm.w_suf[lane] = se;
-        }
-        if (lane == 0) sm.total = tot;
-    }
-    Sync::sync();
-    const long long N = sm.total;
-    long long c_before = __shfl_up_sync(0xffffffffu, ci, 1);
-    F2 w_before = shfl_up_f2(pi, 1);
-    F2 w_after = shfl_down_f2(si, 1);
-    if (lane == 0) { c_before = 0; w_before = F2{0.f, 0.f}; }
-    if (lane == 31) w_after = F2{0.f, 0.f};
-    c_before += sm.cnt_pre[warp];
-    w_before = f2_add(sm.w_pre[warp], w_before);
-    w_after = f2_add(w_after, sm.w_suf[warp]);
-
-    // ---- objective at each level of this thread, right to left (class-2
-    // sums from the right)
-    const F2 qm1 = two_sum(q, -1.0f);
-    Top tp{{-INFINITY, 0.f}, -1, 0.f, -INFINITY};
-    {
-        long long na = c_before + c;    // class-1 count through level base + 7
-        F2 rs{0.f, 0.f};                // terms of this thread's levels right of k
-#pragma unroll
-        for (int k = kBinsPerThread - 1; k >= 0; --k) {
-            const long long nb = N - na;
-            if (hv[k] > 0 && nb > 0) {
-                const float2 qa = sQ[base + k];
-                const F2 QA = f2_add(w_before, F2{qa.x, qa.y});
-                const F2 QB = f2_add(rs, w_after);
-                F2 phi;
-                float band;
-                if (shannon) {
-                    const F2 la = df_log2_count<false>((unsigned)na, T), lb = df_log2_count<false>((unsigned)nb, T);
-                    const F2 sa = df_div(QA, df_from_u32((unsigned)na)), sb = df_div(QB, df_from_u32((unsigned)nb));
-                    phi = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
-                    band = shannon_band_df(la.hi, sa.hi, lb.hi, sb.hi);
-                } else {
-                    const float2 pa = __ldg(Tp + na), pb = __ldg(Tp + nb);
-                    const F2 ab = df_mul(df_div(QA, F2{pa.x, pa.y}), df_div(QB, F2{pb.x, pb.y}));
-                    phi = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), qm1);
-                    band = tsallis_band_df(ab.hi, phi.hi, q);
-                }
-                tp = top_merge(Top{phi, base + k, band, -INFINITY}, tp);
-            }
-            const float2 wk = sW[base + k];
-            rs = f2_add(F2{wk.x, wk.y}, rs);
-            na -= hv[k];
-        }
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) tp = top_merge(tp, shfl_top(tp, d));
-    if (lane == 0) {
-        sm.top_vh[warp] = tp.v.hi;
-        sm.top_vl[warp] = tp.v.lo;
-        sm.top_i[warp] = tp.i;
-        sm.top_band[warp] = tp.band;
-        sm.top_u2[warp] = tp.u2;
-    }
-    Sync::sync();
-    Top g = block_top_of(sm);
-    if (g.i < 0) {
-        Sync::sync();
-        return SearchResult{-1, 0.f, TSALLIS_ERR_NO_VALID_THRESHOLD};
-    }
-    if (!(g.u2 >= g.v.hi - g.band)) {
-        Sync::sync();   // sW / sQ may be reused by the caller after this
-        return SearchResult{g.i, g.v.hi + g.v.lo, TSALLIS_OK};
-    }
-
-    // ---- near ties: FP64 from the same double-float sums and powers
-    const float lower = g.v.hi - g.band;
-    double bv = -INFINITY;
-    int bi = -1;
-    {
-        long long na = c_before + c;
-        F2 rs{0.f, 0.f};
-        for (int k = kBinsPerThread - 1; k >= 0; --k) {
-            const long long nb = N - na;
-            if (hv[k] > 0 && nb > 0) {
-                const float2 qa = sQ[base + k];
-                const F2 QA = f2_add(w_before, F2{qa.x, qa.y});
-                const F2 QB = f2_add(rs, w_after);
-                F2 phi;
-                float band;
-                double f;
-                if (shannon) {
-                    const F2 la = df_log2_count<false>((unsigned)na, T), lb = df_log2_count<false>((unsigned)nb, T);
-                    const F2 sa = df_div(QA, df_from_u32((unsigned)na)), sb = df_div(QB, df_from_u32((unsigned)nb));
-                    phi = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
-                    band = shannon_band_df(la.hi, sa.hi, lb.hi, sb.hi);
-                    f = 0.6931471805599453 * ((df_to_double(la) - df_to_double(QA) / (double)na) +
-                                              (df_to_double(lb) - df_to_double(QB) / (double)nb));
-                } else {
-                    const float2 pa = __ldg(Tp + na), pb = __ldg(Tp + nb);
-                    const F2 ab = df_mul(df_div(QA, F2{pa.x, pa.y}), df_div(QB, F2{pb.x, pb.y}));
-                    phi = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), qm1);
-                    band = tsallis_band_df(ab.hi, phi.hi, q);
-                    f = (1.0 - (df_to_double(QA) / ((double)pa.x + (double)pa.y)) *
-                                   (df_to_double(QB) / ((double)pb.x + (double)pb.y))) /
-                        ((double)q - 1.0);
-                }
-                if (phi.hi + band >= lower) argmax_merge(bv, bi, f, base + k);
-            }
-            const float2 wk = sW[base + k];
-            rs = f2_add(F2{wk.x, wk.y}, rs);
-            na -= hv[k];
-        }
-    }
-    block_argmax_d<Sync>(bv, bi, sm);
-    const int t_win = sm.red_i[0];
-    const float phi_win = (float)sm.red_dv[0];
-    Sync::sync();
-    return SearchResult{t_win, phi_win, TSALLIS_OK | TSALLIS_STATUS_RERANKED};
-}
-
-// ------------------------------------------------------------ fast table search
-//
-// The table search (above) for a histogram whose total count N is that of
-// the term table Tp, over the compacted list of its non-empty levels, with
-// the table reads of a thread issued together: the terms Tp[h_i] for the
-// class sums, then the class powers Tp[N_1] and Tp[N_2]. The arithmetic is
-// the table search's: class-1 and (separately) class-2 double-float sums,
-// the objective in double-float with an error bound at every non-empty
-// level with a non-empty class 2, the smallest level on equal values, and
-// FP64 for the levels whose bound reaches the maximum's. Four barriers (six
-// with a re-rank), against the dozen of search1d_block, and no transcendental
+// The exhaustive search for a histogram whose total count N is fixed in
+// advance (one slice of known size): the double-float terms 2^64 (n / N)^q
+// for every count n = 0..N are read from a table (Tp, built once per N and
+// q; at q = 1 the table holds n log2 n). The non-empty levels are compacted
+// first (an empty level gives the same partition as the non-empty level
+// below it, whose value is the smaller t), so each thread evaluates a short
+// run of entries, and a thread's table reads are issued together: the terms
+// Tp[h_i] for the class sums, then the class powers Tp[N_1] and Tp[N_2].
+// Class-1 and (separately, from the right) class-2 sums in double-float, the
+// objective in double-float with an error bound at every non-empty level
+// with a non-empty class 2, the smallest level on equal values, and FP64 for
+// the levels whose bound reaches the maximum's. Four barriers (six with a
+// re-rank), against the dozen of search1d_block, and no transcendental
 // functions but log2 at q = 1. Scratch (shared memory): sIC[kMaxBins]
 // (level, count) and sW[kMaxBins] (terms).
 template <class Sync>

@@ -599,8 +599,7 @@ __global__ void __launch_bounds__(kBlockThreads, kSegMinBlocks) k_segment1d(cons
                         __threadfence();
                         SearchResult r =
                             (a.ptab != nullptr && gn == a.ptab_n && a.curve == nullptr)
-                                ? search1d_table<WorkSync>(gh, a.L, a.q, a.ptab, ssm, sT,
-                                                           reinterpret_cast<float2*>(sIC), dft)
+                                ? search1d_fast<WorkSync>(gh, a.L, a.q, a.ptab, a.ptab_n, ssm, sIC, sT, dft)
                                 : search1d_block<WorkSync>(
                                       gh, a.L, a.q, a.curve ? a.curve + (long long)w.group * (a.L - 1) : nullptr,
                                       ssm, sT, sIC, dft);
