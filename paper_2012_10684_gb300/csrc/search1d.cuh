@@ -443,13 +443,28 @@ __device__ SearchResult search1d_fast(const int32_t* __restrict__ h, int L, floa
     if (lane == 0) { c_before = 0; w_before = F2{0.f, 0.f}; }
     if (lane == 31) w_after = F2{0.f, 0.f};
     {
-        F2 pw{0.f, 0.f}, sw{0.f, 0.f};
-        long long cw = 0;
-        for (int w = 0; w < warp; ++w) { cw += sm.cnt_pre[w]; pw = f2_add(pw, sm.w_pre[w]); }
-        for (int w = kSearchWarps - 1; w > warp; --w) sw = f2_add(sm.w_suf[w], sw);
-        c_before += cw;
-        w_before = f2_add(pw, w_before);
-        w_after = f2_add(w_after, sw);
+        // the 16 warps' totals scanned in four shuffle rounds (lane l holds
+        // warp l mod 16's), then this warp's exclusive prefix and suffix
+        const int wl = lane & (kSearchWarps - 1);
+        long long cw = sm.cnt_pre[wl];
+        F2 pw = sm.w_pre[wl], sw = sm.w_suf[wl];
+#pragma unroll
+        for (int d = 1; d < kSearchWarps; d <<= 1) {
+            const long long oc = __shfl_up_sync(0xffffffffu, cw, d);
+            const F2 op = shfl_up_f2(pw, d);
+            const F2 os = shfl_down_f2(sw, d);
+            if (wl >= d) { cw += oc; pw = f2_add(op, pw); }
+            if (wl + d < kSearchWarps) sw = f2_add(sw, os);
+        }
+        const int lp = (warp + kSearchWarps - 1) & (kSearchWarps - 1), ls = (warp + 1) & (kSearchWarps - 1);
+        const long long cx = __shfl_sync(0xffffffffu, cw, lp);
+        const F2 px{__shfl_sync(0xffffffffu, pw.hi, lp), __shfl_sync(0xffffffffu, pw.lo, lp)};
+        const F2 sx{__shfl_sync(0xffffffffu, sw.hi, ls), __shfl_sync(0xffffffffu, sw.lo, ls)};
+        if (warp > 0) {
+            c_before += cx;
+            w_before = f2_add(px, w_before);
+        }
+        if (warp < kSearchWarps - 1) w_after = f2_add(w_after, sx);
     }
     // class-2 sums from the right: sW[j] becomes Q_2 at entry j
     {
