@@ -273,7 +273,7 @@ def batch_leg(dev, steps=20, warmup=3, nvol=64, dmax=600):
                         "basis": "algorithmic bytes (the volume read twice and the mask written); the tail of each "
                                  "volume's second read hits L2, so DRAM moves fewer bytes and frac can exceed 1"}}
     res["proposer"] = proposer_legs(dev, vols, masks, outs, outs[0].clone())
-    tg.set_launch_shape(65536, 0)
+    tg.set_launch_shape()
     del vols, masks, g
     torch.cuda.empty_cache()
     return res

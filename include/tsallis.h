@@ -159,7 +159,7 @@ tsallis_status tsallis_set_wait_timeout(tsallis_ctx* ctx, uint64_t ns);
 /*
  * Launch shape of the persistent kernels (the counterpart of the grid/block
  * tuning in the paper's Table 4): voxels per work tile (a multiple of 8 in
- * 4096..2^22; default 65536) and resident blocks per SM used for the grid
+ * 4096..2^22; default 131072) and resident blocks per SM used for the grid
  * (0 = as many as fit). Returns TSALLIS_ERR_INVALID_ARG outside those ranges.
  */
 tsallis_status tsallis_set_launch_shape(tsallis_ctx* ctx, int32_t tile_vox, int32_t blocks_per_sm);

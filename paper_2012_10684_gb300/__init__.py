@@ -179,8 +179,12 @@ def set_wait_timeout(ns: int, device=None) -> None:
     _check("tsallis_set_wait_timeout", lib().tsallis_set_wait_timeout(context(device), int(ns)))
 
 
-def set_launch_shape(tile_vox: int = 65536, blocks_per_sm: int = 0, device=None) -> None:
-    """Launch shape of the persistent kernels (see tsallis_set_launch_shape)."""
+DEFAULT_TILE_VOX = 131072   # a context's voxels per work tile until set_launch_shape changes it
+
+
+def set_launch_shape(tile_vox: int = DEFAULT_TILE_VOX, blocks_per_sm: int = 0, device=None) -> None:
+    """Launch shape of the persistent kernels (see tsallis_set_launch_shape);
+    without arguments, the defaults."""
     _check("tsallis_set_launch_shape",
            lib().tsallis_set_launch_shape(context(device), int(tile_vox), int(blocks_per_sm)))
 

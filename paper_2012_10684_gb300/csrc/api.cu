@@ -52,7 +52,7 @@ struct tsallis_ctx {
     unsigned long long timeout_ns = 1000000000ull;
     // launch shape of the 1-D persistent kernel
     int copies = 1;
-    int tile_vox = 65536;
+    int tile_vox = 131072;
     int blocks_per_sm = 0;        // resident blocks per SM used for the grid
     int max_blocks_per_sm = 0;    // what the occupancy calculator allows
     // batch work list (device copy) and its host image

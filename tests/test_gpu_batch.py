@@ -138,7 +138,7 @@ def test_batch_autotune_picks_a_valid_shape_and_keeps_results():
         out = tg.tsallis_segment_batch(vols, p)
         assert torch.equal(out[1], ref[0]) and torch.equal(out[2], ref[1])
     finally:
-        tg.set_launch_shape(65536, 0)
+        tg.set_launch_shape()
     _check_batch(vols_np, "volume", 0.8)
 
 
@@ -154,7 +154,7 @@ def test_batch_autotune_cache(tmp_path):
         first = tg.tsallis_autotune_batch(vols, p, cache=cache)
         entries = tg.autotune_cache_load(cache)
         assert len(entries) == 1 and list(entries.values())[0]["tile_vox"] == first[0]
-        tg.set_launch_shape(65536, 0)
+        tg.set_launch_shape()
         import time
         t0 = time.time()
         second = tg.tsallis_autotune_batch(vols, p, cache=cache)
@@ -162,7 +162,7 @@ def test_batch_autotune_cache(tmp_path):
         tg.tsallis_autotune_batch(vols[:2], p, cache=cache)
         assert len(tg.autotune_cache_load(cache)) == 2
     finally:
-        tg.set_launch_shape(65536, 0)
+        tg.set_launch_shape()
 
 
 def test_batch_argument_errors():

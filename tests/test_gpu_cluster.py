@@ -96,7 +96,7 @@ def test_first_pass_prediction_that_fails_falls_back_exactly():
         try:
             _, st = _check_step(v, "slice", 0.8)
         finally:
-            tg.set_launch_shape(65536, 0)
+            tg.set_launch_shape()
     first = (st & tg.TSALLIS_STATUS_FIRST_PASS_EXACT) != 0
     assert first.sum() < nz
 

@@ -38,7 +38,7 @@ def _predict_kernel():
     tg.set_slice_kernel("predict")
     yield
     tg.set_prediction(8, 8)
-    tg.set_launch_shape(65536, 0)
+    tg.set_launch_shape()
     tg.withhold_predictions(False)
     tg.set_slice_kernel("auto")
 
