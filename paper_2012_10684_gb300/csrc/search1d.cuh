@@ -511,29 +511,32 @@ __device__ SearchResult search1d_fast(const int32_t* __restrict__ h, int L, floa
                 if (nb <= 0) continue;
                 const float2 qb2 = sW[j];
                 const F2 QB{qb2.x, qb2.y};
-                F2 phi;
+                F2 phi, la{0.f, 0.f}, lb{0.f, 0.f};
                 float band;
-                double f = 0.0;
                 if (shannon) {
-                    const F2 la = df_log2_count<true>((unsigned)na, T), lb = df_log2_count<true>((unsigned)nb, T);
+                    la = df_log2_count<true>((unsigned)na, T);
+                    lb = df_log2_count<true>((unsigned)nb, T);
                     const F2 sa = df_div(qa, df_from_u32((unsigned)na)), sb = df_div(QB, df_from_u32((unsigned)nb));
                     phi = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
                     band = shannon_band_df(la.hi, sa.hi, lb.hi, sb.hi);
-                    if (mode == 1)
-                        f = 0.6931471805599453 * ((df_to_double(la) - df_to_double(qa) / (double)na) +
-                                                  (df_to_double(lb) - df_to_double(QB) / (double)nb));
                 } else {
                     const F2 ab = df_mul(df_div(qa, F2{pa[u].x, pa[u].y}), df_div(QB, F2{pb[u].x, pb[u].y}));
                     phi = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), qm1);
                     band = tsallis_band_df(ab.hi, phi.hi, q);
-                    if (mode == 1)
-                        f = (1.0 - (df_to_double(qa) / ((double)pa[u].x + (double)pa[u].y)) *
-                                       (df_to_double(QB) / ((double)pb[u].x + (double)pb[u].y))) /
-                            ((double)q - 1.0);
                 }
                 const int lev = sIC[j].x;
-                if (mode == 0) tp = top_merge(Top{phi, lev, band, -INFINITY}, tp);
-                else if (phi.hi + band >= lower) argmax_merge(bv, bi, f, lev);
+                if (mode == 0) {
+                    tp = top_merge(Top{phi, lev, band, -INFINITY}, tp);
+                } else if (phi.hi + band >= lower) {
+                    // FP64 (a slow pipe here) only for the entries the bounds leave in play
+                    const double f =
+                        shannon ? 0.6931471805599453 * ((df_to_double(la) - df_to_double(qa) / (double)na) +
+                                                        (df_to_double(lb) - df_to_double(QB) / (double)nb))
+                                : (1.0 - (df_to_double(qa) / ((double)pa[u].x + (double)pa[u].y)) *
+                                             (df_to_double(QB) / ((double)pb[u].x + (double)pb[u].y))) /
+                                      ((double)q - 1.0);
+                    argmax_merge(bv, bi, f, lev);
+                }
             }
         }
     };
