@@ -786,10 +786,14 @@ __device__ SearchResult search1d_window(const int32_t* __restrict__ h, int L, fl
             if (valid && ((ws.sel[base + k] & 2) || fb)) {
                 F2 phi;
                 float band;
-                double f = 0.0;
-                eval(k, na, QA, QB, phi, band, mode == 2 ? &f : nullptr);
-                if (mode < 2) tp = top_merge(Top{phi, base + k, band, -INFINITY}, tp);
-                else if (phi.hi + band >= lower) argmax_merge(bv, bi, f, base + k);
+                eval(k, na, QA, QB, phi, band, nullptr);
+                if (mode < 2) {
+                    tp = top_merge(Top{phi, base + k, band, -INFINITY}, tp);
+                } else if (phi.hi + band >= lower) {
+                    double f = 0.0;   // FP64 only inside the bounds (the same phi and band again)
+                    eval(k, na, QA, QB, phi, band, &f);
+                    argmax_merge(bv, bi, f, base + k);
+                }
             }
             const float2 wk = sW[base + k];
             rs = f2_add(F2{wk.x, wk.y}, rs);
