@@ -480,6 +480,8 @@ __device__ SearchResult search1d_fast(const int32_t* __restrict__ h, int L, floa
     // the left), terms and class powers gathered two entries at a time;
     // mode 1 takes the entries whose bound reaches `lower` in FP64 (re-rank)
     const F2 qm1 = two_sum(q, -1.0f);
+    // 1 / (q - 1) once, so that each objective multiplies instead of dividing
+    const F2 rqm1 = shannon ? F2{0.f, 0.f} : df_div(F2{1.0f, 0.f}, qm1);
     auto sweep = [&](int mode, float lower, Top& tp, double& bv, int& bi) {
         F2 qa = w_before;
         long long na = c_before;
@@ -516,12 +518,14 @@ __device__ SearchResult search1d_fast(const int32_t* __restrict__ h, int L, floa
                 if (shannon) {
                     la = df_log2_count<true>((unsigned)na, T);
                     lb = df_log2_count<true>((unsigned)nb, T);
-                    const F2 sa = df_div(qa, df_from_u32((unsigned)na)), sb = df_div(QB, df_from_u32((unsigned)nb));
+                    const F2 sa = df_div_fast(qa, df_from_u32((unsigned)na)),
+                             sb = df_div_fast(QB, df_from_u32((unsigned)nb));
                     phi = df_mul(df_add(df_add(la, f2_neg(sa)), df_add(lb, f2_neg(sb))), df_ln2());
                     band = shannon_band_df(la.hi, sa.hi, lb.hi, sb.hi);
                 } else {
-                    const F2 ab = df_mul(df_div(qa, F2{pa[u].x, pa[u].y}), df_div(QB, F2{pb[u].x, pb[u].y}));
-                    phi = df_div(df_add(F2{1.0f, 0.f}, f2_neg(ab)), qm1);
+                    const F2 ab =
+                        df_mul(df_div_fast(qa, F2{pa[u].x, pa[u].y}), df_div_fast(QB, F2{pb[u].x, pb[u].y}));
+                    phi = df_mul(df_add(F2{1.0f, 0.f}, f2_neg(ab)), rqm1);
                     band = tsallis_band_df(ab.hi, phi.hi, q);
                 }
                 const int lev = sIC[j].x;

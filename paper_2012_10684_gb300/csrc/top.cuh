@@ -19,6 +19,18 @@ __device__ __forceinline__ F2 df_div(F2 x, F2 y) {
     return fast_two_sum(q1, q2);
 }
 
+// x / y as df_div, with the fast float quotient (__fdividef, within 2 ulp)
+// in both steps: the correction step still recovers the double-float
+// quotient, whose relative error grows from about 2^-47 to a few 2^-45, far
+// inside the bounds below. For normal |y| < 2^126 (the searches' class
+// powers 2^64 (n/N)^q and counts).
+__device__ __forceinline__ F2 df_div_fast(F2 x, F2 y) {
+    const float q1 = __fdividef(x.hi, y.hi);
+    const F2 r = df_add(x, f2_neg(df_mul_f(y, q1)));
+    const float q2 = __fdividef(r.hi, y.hi);
+    return fast_two_sum(q1, q2);
+}
+
 __device__ __forceinline__ bool df_gt(F2 a, F2 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 
 // Running top of (value, level) pairs: the largest value (smallest level on
@@ -58,8 +70,9 @@ __device__ __forceinline__ Top shfl_top(Top t, int d) {
 // Bounds on the error of the double-float objective. Terms (h/N)^q and the
 // class powers are within 1e-12 relative (dfmath.cuh); a double-float sum
 // of at most 4096 positive terms adds at most 4096 * 2^-47 < 3e-11
-// relative; the quotients and products add a few 2^-47. So a b' is within
-// about 7e-11 relative, and the bounds below (1e-10) cover it.
+// relative; the quotients and products add a few 2^-47 (a few 2^-45 with
+// df_div_fast). So a b' is within about 7e-11 relative, and the bounds below
+// (1e-10) cover it.
 __device__ __forceinline__ float tsallis_band_df(float ab, float phi, float q) {
     return 1e-10f * fabsf(ab) / fabsf(q - 1.0f) + 1e-12f * fabsf(phi) + 1e-30f;
 }
