@@ -567,8 +567,9 @@ def copy_bound(dev, h_vol, h_mask, d_vol, d_mask, reps=20):
 def per_slice_legs(dev, vols, masks, outs, args, steps=200, warmup=10):
     """The rest of the 512x512x400 workload (two alternated volumes): per-slice
     thresholds at q = 0.5 and 1.5, each per-slice kernel at q = 0.8, the
-    two-pass floor (histogram, search and binarise as three calls), whole-
-    volume thresholds at every q, and the single 512x512 slice."""
+    same step as three calls (histogram, search and binarise; the volume read
+    twice from HBM), whole-volume thresholds at every q, and the single
+    512x512 slice."""
     import torch
 
     import phantom
@@ -592,7 +593,7 @@ def per_slice_legs(dev, vols, masks, outs, args, steps=200, warmup=10):
                      "ok": bool(((st & 0xff) == 0).all().item())}
     tg.set_slice_kernel("auto")
     res["slice_kernels_q0.8"] = out
-    # the two-pass floor: every slice histogram, the 400 searches, the binarise pass
+    # the step as three calls: every slice histogram, the 400 searches, the binarise pass
     p = tg.tsallis_params(q=Q, mode="slice")
     hs = [tg.tsallis_histogram(v, p) for v in vols]
     ts = [tg.tsallis_search(h, p)[0] for h in hs]
