@@ -859,6 +859,7 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_final(const S2Args a) {
 
 // ------------------------------------------------------------ host side
 
+// The band, then the row-staging ring (used by the per-slice form only; one size for every form).
 int hist2d_smem_bytes(int L2) { return ((L2 * kBandStride + 3) & ~3) * (int)sizeof(int) + kStageBytes; }
 
 cudaError_t seg2d_prepare() {
